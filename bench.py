@@ -1,0 +1,332 @@
+"""Benchmark: exhaustive MACCS-166 similarity search with exact top-k on GB300.
+
+Workload (default): 95,417,114 synthetic MACCS-166 fingerprints (seeded
+generator, seed 0; the paper's library size, Sec. 2.2), 16 independent single
+queries (generator seed 1001) run one after another, k = 30, popcount scan
+with popcount-bucket pruning.  One step = those 16 searches.  Metric:
+G-comparisons/s = queries x records / time.
+
+--impl reference times the CPU oracle (the plain restatement of Fig. 3) on
+this machine's host cores on a bounded sample of the same workload.
+
+Under torchrun (N > 1) each rank holds its own replica of the library and runs
+its own 16 queries (weak scaling, no collective on the data path); the timed
+region is bracketed by barriers and the slowest rank's time is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PAPER_N = 95_417_114
+K = 30
+QUERIES_PER_STEP = 16
+METRIC = "fingerprints x queries / sec (G-comparisons/s), exact top-k"
+UNIT = "G-comparisons/s"
+# The paper: 95,417,114 molecules searched in about 40 minutes (Sec. 2.2).
+PAPER_GCPS = PAPER_N / (40 * 60) / 1e9
+SCAN_SRC = os.path.join(ROOT, "paper_1906_06170_gb300", "csrc", "fps_scan.cu")
+PROFILE = os.path.join(ROOT, "profiles", "scan_single_popc_95M.md")
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--n", type=int, default=PAPER_N, help="library records")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ------------------------------------------------------------------- clocks
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------- roofline
+def measured_peak_gbs():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def profile_traffic():
+    """Per-launch DRAM bytes of the scan kernel from the committed ncu summary, if it
+    was taken on the current kernel source (matching hash); else None."""
+    try:
+        text = open(PROFILE).read()
+    except OSError:
+        return None
+    src_hash = hashlib.sha256(open(SCAN_SRC, "rb").read()).hexdigest()[:16]
+    traffic, h = None, None
+    for line in text.splitlines():
+        if line.startswith("source_sha256_16:"):
+            h = line.split(":", 1)[1].strip()
+        if line.startswith("dram_bytes_per_launch:"):
+            traffic = float(line.split(":", 1)[1].strip())
+    return traffic if (h == src_hash and traffic) else None
+
+
+# ------------------------------------------------------------ cpu baseline
+def cpu_oracle_throughput(records: int, nq: int, seconds_hint: str):
+    """Time the CPU oracle (parse + character compares + full sort) on a bounded sample."""
+    import oracle
+    import synth
+
+    threads = os.cpu_count() or 1
+    text = synth.text_buffer(records, 0)
+    qs = synth.packed_to_strings(synth.packed(nq, 1001))
+    oracle.topk(text[: 1000 * synth.LINE_BYTES], qs[0], K, threads=threads)   # load/compile
+    t0 = time.perf_counter()
+    for q in qs:
+        oracle.topk(text, q, K, threads=threads)
+    dt = time.perf_counter() - t0
+    return {"value": records * nq / dt / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{nq} queries x {records:,} records of the same generator (parse + distances on "
+                      f"{threads} threads + full sort), {dt:.1f} s{seconds_hint}"}
+
+
+# -------------------------------------------------------------- reference
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    records = min(args.n, 2_000_000)
+    import oracle
+    import synth
+
+    threads = os.cpu_count() or 1
+    text = synth.text_buffer(records, 0)
+    qs = synth.packed_to_strings(synth.packed(args.warmup + args.steps, 1001))
+    for q in qs[: args.warmup]:
+        oracle.topk(text, q, K, threads=threads)
+    t0 = time.perf_counter()
+    for q in qs[args.warmup:]:
+        oracle.topk(text, q, K, threads=threads)
+    dt = time.perf_counter() - t0
+    value = records * args.steps / dt / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": value / PAPER_GCPS, "dtype": "u8",
+            "data": "synthetic",
+            "config": {"workload": f"CPU oracle, one query per step over {records:,} of the {args.n:,} "
+                                   f"generated records, k={K}", "n_records": args.n, "k": K},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"1 query x {records:,} records per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ gb300
+def run_gb300(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1906_06170_gb300 as fps
+    import synth
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    n = args.n
+    packed = synth.packed(n, 0)
+    lib = fps.fps_library_load(packed=packed, device=local)
+    info = fps.fps_library_info_get(lib)
+    del packed
+    qs = synth.packed(QUERIES_PER_STEP * ws, 1001)[rank * QUERIES_PER_STEP:(rank + 1) * QUERIES_PER_STEP]
+    qd = torch.from_numpy(qs.view(np.int64).copy()).to(dev)
+    oi = torch.empty((QUERIES_PER_STEP, K), dtype=torch.int32, device=dev)
+    od = torch.empty((QUERIES_PER_STEP, K), dtype=torch.int32, device=dev)
+    oc = torch.empty((QUERIES_PER_STEP,), dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(events=None):
+        for j in range(QUERIES_PER_STEP):
+            if events is not None:
+                events[2 * j].record(stream)
+            fps.fps_search_packed(lib, qd[j], K, out_index=oi[j], out_dist=od[j], out_count=oc[j], stream=stream)
+            if events is not None:
+                events[2 * j + 1].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    fps.fps_sync(lib, stream)
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- timed region (device-resident inputs and outputs)
+    clocks = ClockSampler(local)
+    clocks.start()
+    per_launch = [[torch.cuda.Event(enable_timing=True) for _ in range(2 * QUERIES_PER_STEP)]
+                  for _ in range(args.steps)]
+    barrier()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for s in range(args.steps):
+        step(per_launch[s])
+    t_end.record(stream)
+    barrier()
+    clk = clocks.stop()
+    fps.fps_sync(lib, stream)
+    ms = t_start.elapsed_time(t_end)
+    launch_ms = [per_launch[s][2 * j].elapsed_time(per_launch[s][2 * j + 1])
+                 for s in range(args.steps) for j in range(QUERIES_PER_STEP)]
+    if ws > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # sanity of the last step's results (full parity is in the test suite)
+    cnt = oc.cpu().numpy()
+    dd = od.cpu().numpy()
+    assert np.all(cnt == min(K, n)) and np.all(np.diff(dd, axis=1) >= 0), "bench results malformed"
+
+    # ---- end to end through the C ABI with host buffers (copies inside the timed region)
+    qs_host = qs.copy()
+    e2e_steps = max(2, min(args.steps, 5))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for j in range(QUERIES_PER_STEP):
+            fps.fps_search_packed(lib, qs_host[j], K)
+    barrier()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if ws > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    if rank == 0:
+        units = ws * QUERIES_PER_STEP * n
+        value = units / (ms / args.steps / 1e3) / 1e9
+        e2e_value = units / e2e_s / 1e9
+        # algorithmic bytes of the bucketed scan: every record whose popcount bucket is
+        # within the final k-th distance of the query, 24 B each, plus k result keys
+        bc = info["bucket_count"]
+        pq = np.unpackbits(qs.view(np.uint8), axis=1, bitorder="little")[:, :166].sum(1)
+        tk = dd[:, -1]
+        alg = []
+        for j in range(QUERIES_PER_STEP):
+            lo, hi = max(0, pq[j] - tk[j]), min(166, pq[j] + tk[j])
+            alg.append(24.0 * bc[lo:hi + 1].sum() + 8.0 * K)
+        alg_bytes = float(np.mean(alg))
+        avg_launch_s = float(np.mean(launch_ms)) / 1e3
+        peak, peak_kind = measured_peak_gbs()
+        achieved = alg_bytes / avg_launch_s / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": profile_traffic(), "kernel": "scan_single_kernel<16,256>",
+                "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_launch_s * 1e3,
+                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                else "fallback 6.8 TB/s"}
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": value / PAPER_GCPS,
+                "vs_baseline_note": "paper: 95,417,114 molecules in ~40 min on an i5-6500 (Sec. 2.2); "
+                                    "other hardware, PubChem data -- context only",
+                "dtype": "u64", "data": "synthetic",
+                "config": {"workload": f"{n:,} generated MACCS-166 fingerprints (seed 0), "
+                                       f"{QUERIES_PER_STEP} sequential single queries per step per GPU "
+                                       f"(seed 1001), k={K}, popcount scan with bucket pruning",
+                           "n_records": n, "queries_per_step": QUERIES_PER_STEP, "k": K,
+                           "l2": f"library {info['n_tiles'] * 3072 / 1e9:.2f} GB >> 129 MB L2: every "
+                                 "step streams from HBM, no flush needed",
+                           "parallelism": f"replicas x{ws}"},
+                "roofline": roof, "clocks": clk,
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": QUERIES_PER_STEP * 32,
+                        "d2h_bytes_per_step": QUERIES_PER_STEP * (8 + 8 * K)},
+                "gpu_launches": args.steps * QUERIES_PER_STEP}
+        if not args.no_cpu_baseline and ws == 1:
+            line["cpu_baseline"] = cpu_oracle_throughput(2_000_000, 4, "")
+        print(json.dumps(line), flush=True)
+    fps.fps_release(lib)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gb300(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,206 @@
+/*
+ * fps.h -- C ABI of the GB300 exact fingerprint search (FPScreen hot path).
+ *
+ * The paper (Sec. 4.3, Fig. 3) searches a library of MACCS-166 fingerprints
+ * for the molecules closest to a target: Manhattan distance over the 166
+ * 0/1 keys, every library row paired with its distance, all pairs sorted
+ * ascending, first k returned with their PubChem CIDs ("Input: target
+ * MACCS166, library file F ... Output: CID ... and distance").  Here the
+ * library is parsed once, packed to 24-byte records and kept in GPU memory;
+ * each search is an exhaustive scan plus an exact top-k on the GPU.
+ *
+ * Result order (every path, every size): ascending distance, ties broken by
+ * ascending 0-based library index.  This is a total order, so the answer is
+ * unique and every path returns exactly the same bytes.
+ *
+ * Conventions shared by every entry point:
+ *   - every function returns an fps_status; nothing throws or aborts across
+ *     the ABI;
+ *   - the library handle owns all of its device memory (packed records,
+ *     index permutation, per-stream workspaces) until fps_release;
+ *   - the caller owns every query and result buffer it passes in;
+ *   - a handle is read-only after loading, so searches may run concurrently
+ *     on different CUDA streams; searches on one stream run in stream order.
+ *     fps_release must not race searches still in flight (the caller's duty);
+ *   - bit order of a packed record or query: key j (character j of the text
+ *     line, 0-based) is bit j % 64 of 64-bit word j / 64; bits 166..191 are 0;
+ *   - k = 0 is valid and returns no results; out_count = min(k, N); result
+ *     slots past out_count are left untouched;
+ *   - k may not exceed FPS_K_MAX (FPS_ERR_UNSUPPORTED otherwise).
+ */
+#ifndef FPS_H
+#define FPS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FPS_BITS 166          /* MACCS keys per fingerprint (Sec. 4.2) */
+#define FPS_WORDS 3           /* uint64 words per packed record */
+#define FPS_K_MAX 1920        /* largest k any search accepts */
+
+typedef enum {
+  FPS_OK = 0,
+  FPS_ERR_INVALID_ARG = 1,       /* null required pointer, k < 0, Q < 0, bad query characters ... */
+  FPS_ERR_IO = 2,                /* the library file cannot be read */
+  FPS_ERR_PARSE = 3,             /* a library line is malformed (see fps_load_desc.err_line) */
+  FPS_ERR_BUDGET = 4,            /* the library would exceed hbm_budget_bytes; nothing was allocated */
+  FPS_ERR_CUDA = 5,              /* a CUDA runtime call failed (no device, out of memory, launch error) */
+  FPS_ERR_TIMEOUT = 6,           /* a bounded device-side wait ran out; results of that search are invalid */
+  FPS_ERR_OVERFLOW_INTERNAL = 7, /* an internal candidate buffer overflowed and could not be recovered */
+  FPS_ERR_UNSUPPORTED = 8,       /* a valid request this build does not serve (k > FPS_K_MAX, missing operand) */
+  FPS_ERR_NOMEM = 9              /* host allocation failed */
+} fps_status;
+
+typedef struct fps_library_s* fps_library;
+
+/* ---------------------------------------------------------------- loading */
+
+#define FPS_LOAD_ACCEPT_167 0x1u  /* a 167-character line starting with '0' loses that character */
+#define FPS_LOAD_NO_BUCKETS 0x2u  /* keep library order: no popcount buckets, so no pruning */
+#define FPS_LOAD_TC_OPERAND 0x4u  /* also build the 0/1 FP8 operand the tensor-core batch path needs */
+
+/*
+ * Exactly one library source must be given: a file path, an in-memory text
+ * buffer, or already-packed records.
+ *
+ * Text format (Fig. 3 step 1, "obtain all the molecules from F, construct CID,
+ * matrix A"): one molecule per line, either 166 '0'/'1' characters or
+ * "<cid><sep><166 characters>" with sep a space, tab or comma and cid a
+ * non-negative decimal integer.  A trailing '\r' is dropped; the final line
+ * may lack its '\n'.  Any other line -- including an empty line before the
+ * end -- fails the load with FPS_ERR_PARSE and its 1-based number in
+ * *err_line.  Without a CID column the CID of a row is its 0-based index.
+ *
+ * Packed source: n_packed records of FPS_WORDS uint64 each (host memory, bit
+ * order above; pad bits must be zero, else FPS_ERR_INVALID_ARG), with an
+ * optional host array of n_packed CIDs.
+ *
+ * hbm_budget_bytes: 0 = unlimited; otherwise the load fails with
+ * FPS_ERR_BUDGET, before allocating any device memory, if the device bytes
+ * the library needs exceed it.
+ */
+typedef struct {
+  const char* path;              /* library text file, or NULL */
+  const char* text;              /* in-memory library text, or NULL */
+  size_t text_len;
+  const uint64_t* packed;        /* packed records (host), or NULL */
+  size_t n_packed;
+  const int64_t* cids;           /* optional CIDs of the packed records (host), or NULL */
+  int device;                    /* CUDA device ordinal */
+  size_t hbm_budget_bytes;
+  uint32_t flags;                /* FPS_LOAD_* */
+  size_t* err_line;              /* out (optional): line of the first parse error */
+} fps_load_desc;
+
+/* Parse (or take) the library, pack it, lay it out by popcount bucket and copy it to the device. */
+fps_status fps_library_load(const fps_load_desc* desc, fps_library* out);
+
+/* Release a library and all device memory it owns.  NULL is accepted (no-op). */
+fps_status fps_release(fps_library lib);
+
+typedef struct {
+  int64_t n_records;             /* N */
+  int64_t n_tiles;               /* 128-record scan tiles, including bucket padding */
+  size_t device_bytes;           /* device memory held by the library (workspaces excluded) */
+  int device;
+  int bucketed;                  /* 1 = popcount-bucketed layout (pruning on) */
+  int has_tc_operand;            /* 1 = the FP8 tensor-core operand is resident */
+  int64_t bucket_count[FPS_BITS + 1]; /* records per popcount 0..166 */
+} fps_library_info;
+
+fps_status fps_library_info_get(fps_library lib, fps_library_info* info);
+
+/* CID of library row `index` (host lookup). */
+fps_status fps_library_cid(fps_library lib, int64_t index, int64_t* cid);
+
+/* --------------------------------------------------------------- searching */
+
+typedef enum {
+  FPS_PATH_AUTO = 0,     /* let the library choose (autotuned) */
+  FPS_PATH_POPC = 1,     /* popcount scan: one launch per query (single-query kernel) */
+  FPS_PATH_POPC_BATCH = 2, /* popcount scan, many queries per launch */
+  FPS_PATH_TC_FP8 = 3,   /* tensor-core contraction on 0/1 FP8 operands */
+  FPS_PATH_TC_I8 = 4,    /* tensor-core contraction on 0/1 INT8 operands */
+  FPS_PATH_LEARNED = 5   /* predicted per-query threshold, exact fallback */
+} fps_path;
+
+#define FPS_SEARCH_DEVICE_IO 0x1u /* queries, k, offsets and outputs are device pointers; the call only
+                                     enqueues work on the stream and returns (results valid after the
+                                     stream is synchronised; errors reported by fps_sync) */
+
+typedef struct {
+  int64_t queries;               /* queries served by the call */
+  int64_t fallbacks;             /* queries that needed the exact fallback scan */
+  int64_t candidates;            /* candidate keys examined by the final selection */
+  int64_t path_used;             /* fps_path actually run */
+} fps_search_stats;
+
+typedef struct {
+  int path;                      /* fps_path */
+  uint32_t flags;                /* FPS_SEARCH_* */
+  double timeout_s;              /* bound on any device-side wait; <= 0 = 2 s */
+  fps_search_stats* stats;       /* optional out (host-IO calls only) */
+  const float* tau;              /* FPS_PATH_LEARNED: per-query thresholds (host or device like the queries) */
+} fps_search_opts;
+
+/*
+ * The paper's single-molecule search (Fig. 3): query166 is 166 '0'/'1'
+ * characters (FPS_ERR_INVALID_ARG otherwise).  Host outputs, synchronous.
+ * out_index / out_dist receive min(k, N) entries; out_cid (nullable) the
+ * CIDs; *out_count their number.  cuda_stream may be NULL (default stream).
+ */
+fps_status fps_search(fps_library lib, const char* query166, int k, int32_t* out_index, int32_t* out_dist,
+                      int64_t* out_cid, int* out_count, void* cuda_stream);
+
+/*
+ * Single query in packed form (FPS_WORDS words).  Without FPS_SEARCH_DEVICE_IO
+ * every pointer is host memory and the call returns when results are written.
+ * With it, query, out_index, out_dist and out_count are device pointers, the
+ * call is asynchronous on cuda_stream and *out_count is an int32 on the
+ * device.  opts may be NULL (defaults).
+ */
+fps_status fps_search_packed(fps_library lib, const uint64_t* query, int k, int32_t* out_index, int32_t* out_dist,
+                             int32_t* out_count, const fps_search_opts* opts, void* cuda_stream);
+
+/*
+ * Q queries (Q x FPS_WORDS packed words) with per-query k[q].  Results of
+ * query q go to out_index/out_dist[out_offsets[q] .. out_offsets[q] + k[q]),
+ * out_offsets holding Q + 1 entries (out_offsets[q+1] - out_offsets[q] >= k[q]);
+ * out_count[q] = min(k[q], N).  k and out_offsets are always host arrays (the
+ * launch plan is made on the host); queries, out_index, out_dist and
+ * out_count are host or device memory per opts->flags, as in
+ * fps_search_packed.  opts->path selects the kernel (FPS_PATH_AUTO lets the
+ * library choose).
+ */
+fps_status fps_search_batch(fps_library lib, const uint64_t* queries, int Q, const int32_t* k,
+                            const int64_t* out_offsets, int32_t* out_index, int32_t* out_dist, int32_t* out_count,
+                            const fps_search_opts* opts, void* cuda_stream);
+
+/* Wait for cuda_stream and report (then clear) any device-side error of searches enqueued on it. */
+fps_status fps_sync(fps_library lib, void* cuda_stream);
+
+/* ----------------------------------------------------------------- helpers */
+
+const char* fps_status_string(fps_status st);
+
+/* Pack 166 '0'/'1' characters into FPS_WORDS words (host). */
+fps_status fps_pack_query(const char* query166, uint64_t out[FPS_WORDS]);
+
+/*
+ * Host-only parse of library text into packed records (the load's first
+ * step, exposed for tools and tests).  Call with out_packed = NULL to get the
+ * record count in *out_n; otherwise cap records are available at out_packed
+ * (cap x FPS_WORDS words) and out_cids (nullable).
+ */
+fps_status fps_pack_text(const char* text, size_t text_len, uint32_t flags, uint64_t* out_packed,
+                         int64_t* out_cids, size_t cap, size_t* out_n, size_t* err_line);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FPS_H */

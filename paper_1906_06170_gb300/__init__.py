@@ -1,0 +1,315 @@
+"""Python binding of the FPScreen GB300 search library (C ABI in include/fps.h).
+
+Argument marshalling only: every step of a search runs in the CUDA kernels of
+``libfps.so``.  The names mirror the C entry points.  Host inputs are NumPy
+arrays; device inputs/outputs are ``torch`` CUDA tensors (PyTorch supplies
+device memory and streams).  If ``libfps.so`` has not been built the import
+fails loudly -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "libfps.so")
+
+FPS_BITS, FPS_WORDS, FPS_K_MAX = 166, 3, 1920
+(FPS_OK, FPS_ERR_INVALID_ARG, FPS_ERR_IO, FPS_ERR_PARSE, FPS_ERR_BUDGET, FPS_ERR_CUDA, FPS_ERR_TIMEOUT,
+ FPS_ERR_OVERFLOW_INTERNAL, FPS_ERR_UNSUPPORTED, FPS_ERR_NOMEM) = range(10)
+FPS_LOAD_ACCEPT_167, FPS_LOAD_NO_BUCKETS, FPS_LOAD_TC_OPERAND = 0x1, 0x2, 0x4
+(FPS_PATH_AUTO, FPS_PATH_POPC, FPS_PATH_POPC_BATCH, FPS_PATH_TC_FP8, FPS_PATH_TC_I8,
+ FPS_PATH_LEARNED) = range(6)
+FPS_SEARCH_DEVICE_IO = 0x1
+
+if not os.path.exists(_SO):
+    raise ImportError(f"{_SO} is missing: build the CUDA library first (__graft_entry__.build())")
+_lib = ctypes.CDLL(_SO)
+
+
+class FpsError(RuntimeError):
+    def __init__(self, status: int, where: str = "", line: int = 0):
+        msg = _lib.fps_status_string(status).decode()
+        super().__init__(f"{where}: {msg} (status {status})" + (f" at line {line}" if line else ""))
+        self.status = status
+        self.line = line
+
+
+class fps_load_desc(ctypes.Structure):
+    _fields_ = [("path", ctypes.c_char_p), ("text", ctypes.c_void_p), ("text_len", ctypes.c_size_t),
+                ("packed", ctypes.c_void_p), ("n_packed", ctypes.c_size_t), ("cids", ctypes.c_void_p),
+                ("device", ctypes.c_int), ("hbm_budget_bytes", ctypes.c_size_t), ("flags", ctypes.c_uint32),
+                ("err_line", ctypes.POINTER(ctypes.c_size_t))]
+
+
+class fps_library_info(ctypes.Structure):
+    _fields_ = [("n_records", ctypes.c_int64), ("n_tiles", ctypes.c_int64), ("device_bytes", ctypes.c_size_t),
+                ("device", ctypes.c_int), ("bucketed", ctypes.c_int), ("has_tc_operand", ctypes.c_int),
+                ("bucket_count", ctypes.c_int64 * (FPS_BITS + 1))]
+
+
+class fps_search_stats(ctypes.Structure):
+    _fields_ = [("queries", ctypes.c_int64), ("fallbacks", ctypes.c_int64), ("candidates", ctypes.c_int64),
+                ("path_used", ctypes.c_int64)]
+
+
+class fps_search_opts(ctypes.Structure):
+    _fields_ = [("path", ctypes.c_int), ("flags", ctypes.c_uint32), ("timeout_s", ctypes.c_double),
+                ("stats", ctypes.POINTER(fps_search_stats)), ("tau", ctypes.c_void_p)]
+
+
+_vp, _i32, _i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
+_lib.fps_status_string.argtypes = [_i32]
+_lib.fps_status_string.restype = ctypes.c_char_p
+_lib.fps_library_load.argtypes = [ctypes.POINTER(fps_load_desc), ctypes.POINTER(_vp)]
+_lib.fps_release.argtypes = [_vp]
+_lib.fps_library_info_get.argtypes = [_vp, ctypes.POINTER(fps_library_info)]
+_lib.fps_library_cid.argtypes = [_vp, _i64, ctypes.POINTER(_i64)]
+_lib.fps_search.argtypes = [_vp, ctypes.c_char_p, _i32, _vp, _vp, _vp, ctypes.POINTER(_i32), _vp]
+_lib.fps_search_packed.argtypes = [_vp, _vp, _i32, _vp, _vp, _vp, ctypes.POINTER(fps_search_opts), _vp]
+_lib.fps_search_batch.argtypes = [_vp, _vp, _i32, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(fps_search_opts), _vp]
+_lib.fps_sync.argtypes = [_vp, _vp]
+_lib.fps_pack_query.argtypes = [ctypes.c_char_p, _vp]
+_lib.fps_pack_text.argtypes = [_vp, ctypes.c_size_t, ctypes.c_uint32, _vp, _vp, ctypes.c_size_t,
+                               ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]
+for _f in ("fps_library_load", "fps_release", "fps_library_info_get", "fps_library_cid", "fps_search",
+           "fps_search_packed", "fps_search_batch", "fps_sync", "fps_pack_query", "fps_pack_text"):
+    getattr(_lib, _f).restype = _i32
+
+
+def _check(st: int, where: str, line: int = 0):
+    if st != FPS_OK:
+        raise FpsError(st, where, line)
+
+
+def library_path() -> str:
+    return _SO
+
+
+class Library:
+    """A resident library handle (owns its device memory until fps_release)."""
+
+    def __init__(self, handle: int):
+        self.handle = handle
+
+    @property
+    def _h(self):
+        if not self.handle:
+            raise FpsError(FPS_ERR_INVALID_ARG, "released library")
+        return self.handle
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        fps_release(self)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        try:
+            import torch
+
+            if torch.cuda.is_available() and torch.cuda.is_initialized():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return 0
+    return int(getattr(stream, "cuda_stream", stream))
+
+
+def _is_cuda(x):
+    return hasattr(x, "is_cuda") and x.is_cuda
+
+
+def fps_library_load(*, path=None, text=None, packed=None, cids=None, device: int = 0, hbm_budget_bytes: int = 0,
+                     flags: int = 0) -> Library:
+    d = fps_load_desc()
+    keep = []
+    if path is not None:
+        d.path = os.fsencode(path)
+    if text is not None:
+        buf = np.frombuffer(text, dtype=np.uint8) if isinstance(text, (bytes, bytearray)) else \
+            np.ascontiguousarray(text, dtype=np.uint8)
+        keep.append(buf)
+        d.text = buf.ctypes.data if buf.size else ctypes.addressof(ctypes.c_char(0))
+        d.text_len = buf.size
+    if packed is not None:
+        p = np.ascontiguousarray(np.asarray(packed, dtype=np.uint64).reshape(-1, FPS_WORDS))
+        keep.append(p)
+        d.packed = p.ctypes.data if p.size else ctypes.addressof(ctypes.c_uint64(0))
+        d.n_packed = p.shape[0]
+        if cids is not None:
+            c = np.ascontiguousarray(np.asarray(cids, dtype=np.int64))
+            keep.append(c)
+            d.cids = c.ctypes.data
+    d.device, d.hbm_budget_bytes, d.flags = device, hbm_budget_bytes, flags
+    err = ctypes.c_size_t(0)
+    d.err_line = ctypes.pointer(err)
+    h = _vp()
+    st = _lib.fps_library_load(ctypes.byref(d), ctypes.byref(h))
+    _check(st, "fps_library_load", err.value)
+    return Library(h.value)
+
+
+def fps_release(lib: Library):
+    if lib is not None and lib.handle:
+        _check(_lib.fps_release(lib.handle), "fps_release")
+        lib.handle = None
+
+
+def fps_library_info_get(lib: Library) -> dict:
+    info = fps_library_info()
+    _check(_lib.fps_library_info_get(lib._h, ctypes.byref(info)), "fps_library_info_get")
+    return {"n_records": info.n_records, "n_tiles": info.n_tiles, "device_bytes": info.device_bytes,
+            "device": info.device, "bucketed": bool(info.bucketed), "has_tc_operand": bool(info.has_tc_operand),
+            "bucket_count": np.array(info.bucket_count[:], np.int64)}
+
+
+def fps_library_cid(lib: Library, index: int) -> int:
+    c = _i64(0)
+    _check(_lib.fps_library_cid(lib._h, int(index), ctypes.byref(c)), "fps_library_cid")
+    return c.value
+
+
+def fps_search(lib: Library, query166: str, k: int, stream=None):
+    """The paper's single-molecule search: (index, distance, cid) NumPy arrays, ascending."""
+    q = query166.encode() if isinstance(query166, str) else bytes(query166)
+    if len(q) != FPS_BITS:
+        raise FpsError(FPS_ERR_INVALID_ARG, "fps_search: query must have 166 characters")
+    n = max(int(k), 1)
+    idx, dist, cid = np.zeros(n, np.int32), np.zeros(n, np.int32), np.zeros(n, np.int64)
+    cnt = _i32(0)
+    st = _lib.fps_search(lib._h, q, int(k), idx.ctypes.data, dist.ctypes.data, cid.ctypes.data,
+                         ctypes.byref(cnt), _stream_ptr(stream))
+    _check(st, "fps_search")
+    c = cnt.value
+    return idx[:c], dist[:c], cid[:c]
+
+
+def _opts(path, flags, timeout_s, stats, tau_ptr=None):
+    o = fps_search_opts()
+    o.path, o.flags, o.timeout_s = int(path), int(flags), float(timeout_s)
+    if stats is not None:
+        o.stats = ctypes.pointer(stats)
+    if tau_ptr:
+        o.tau = tau_ptr
+    return o
+
+
+def fps_search_packed(lib: Library, query, k: int, *, out_index=None, out_dist=None, out_count=None,
+                      path: int = FPS_PATH_POPC, timeout_s: float = 0.0, stream=None):
+    """Single packed query (3 uint64 words).
+
+    Host form: ``query`` is a NumPy array; returns (index, distance) NumPy arrays.
+    Device form: ``query`` is a CUDA tensor; outputs are CUDA int32 tensors
+    (allocated if not given) and the call is asynchronous on ``stream``;
+    returns (out_index, out_dist, out_count).
+    """
+    if _is_cuda(query):
+        import torch
+
+        dev = query.device
+        if out_index is None:
+            out_index = torch.empty(max(int(k), 1), dtype=torch.int32, device=dev)
+        if out_dist is None:
+            out_dist = torch.empty(max(int(k), 1), dtype=torch.int32, device=dev)
+        if out_count is None:
+            out_count = torch.empty(1, dtype=torch.int32, device=dev)
+        o = _opts(path, FPS_SEARCH_DEVICE_IO, timeout_s, None)
+        st = _lib.fps_search_packed(lib._h, query.data_ptr(), int(k), out_index.data_ptr(), out_dist.data_ptr(),
+                                    out_count.data_ptr(), ctypes.byref(o), _stream_ptr(stream))
+        _check(st, "fps_search_packed")
+        return out_index, out_dist, out_count
+    q = np.ascontiguousarray(np.asarray(query, dtype=np.uint64).reshape(FPS_WORDS))
+    n = max(int(k), 1)
+    idx, dist, cnt = np.zeros(n, np.int32), np.zeros(n, np.int32), np.zeros(1, np.int32)
+    stats = fps_search_stats()
+    o = _opts(path, 0, timeout_s, stats)
+    st = _lib.fps_search_packed(lib._h, q.ctypes.data, int(k), idx.ctypes.data, dist.ctypes.data, cnt.ctypes.data,
+                                ctypes.byref(o), _stream_ptr(stream))
+    _check(st, "fps_search_packed")
+    return idx[: cnt[0]], dist[: cnt[0]]
+
+
+def batch_offsets(k) -> np.ndarray:
+    k = np.asarray(k, dtype=np.int64).reshape(-1)
+    off = np.zeros(k.size + 1, np.int64)
+    off[1:] = np.cumsum(np.maximum(k, 0))
+    return off
+
+
+def fps_search_batch(lib: Library, queries, k, *, path: int = FPS_PATH_AUTO, out_index=None, out_dist=None,
+                     out_count=None, offsets=None, tau=None, timeout_s: float = 0.0, stream=None, stats=None):
+    """Many packed queries (Q x 3 uint64) with per-query k (host array or scalar).
+
+    Host form (NumPy queries): returns a list of (index, distance) per query.
+    Device form (CUDA tensor queries): outputs are CUDA int32 tensors laid out
+    by ``offsets`` (prefix sums of k); asynchronous; returns
+    (out_index, out_dist, out_count, offsets).
+    """
+    Q = int(queries.shape[0]) if hasattr(queries, "shape") else len(queries)
+    kk = np.asarray(k, dtype=np.int32).reshape(-1)
+    if kk.size == 1 and Q != 1:
+        kk = np.full(Q, kk[0], np.int32)
+    kk = np.ascontiguousarray(kk)
+    off = batch_offsets(kk) if offsets is None else np.ascontiguousarray(np.asarray(offsets, np.int64))
+    total = max(int(off[-1]), 1)
+    st_obj = stats if stats is not None else fps_search_stats()
+    if _is_cuda(queries):
+        import torch
+
+        dev = queries.device
+        if out_index is None:
+            out_index = torch.empty(total, dtype=torch.int32, device=dev)
+        if out_dist is None:
+            out_dist = torch.empty(total, dtype=torch.int32, device=dev)
+        if out_count is None:
+            out_count = torch.empty(max(Q, 1), dtype=torch.int32, device=dev)
+        o = _opts(path, FPS_SEARCH_DEVICE_IO, timeout_s, None, tau.data_ptr() if tau is not None else None)
+        st = _lib.fps_search_batch(lib._h, queries.data_ptr(), Q, kk.ctypes.data, off.ctypes.data,
+                                   out_index.data_ptr(), out_dist.data_ptr(), out_count.data_ptr(), ctypes.byref(o),
+                                   _stream_ptr(stream))
+        _check(st, "fps_search_batch")
+        return out_index, out_dist, out_count, off
+    q = np.ascontiguousarray(np.asarray(queries, dtype=np.uint64).reshape(-1, FPS_WORDS))
+    idx, dist, cnt = np.zeros(total, np.int32), np.zeros(total, np.int32), np.zeros(max(Q, 1), np.int32)
+    tau_arr = None
+    if tau is not None:
+        tau_arr = np.ascontiguousarray(np.asarray(tau, np.float32))
+    o = _opts(path, 0, timeout_s, st_obj, tau_arr.ctypes.data if tau_arr is not None else None)
+    st = _lib.fps_search_batch(lib._h, q.ctypes.data, Q, kk.ctypes.data, off.ctypes.data, idx.ctypes.data,
+                               dist.ctypes.data, cnt.ctypes.data, ctypes.byref(o), _stream_ptr(stream))
+    _check(st, "fps_search_batch")
+    return [(idx[off[i]: off[i] + cnt[i]].copy(), dist[off[i]: off[i] + cnt[i]].copy()) for i in range(Q)]
+
+
+def fps_sync(lib: Library, stream=None):
+    _check(_lib.fps_sync(lib._h, _stream_ptr(stream)), "fps_sync")
+
+
+def fps_pack_query(query166: str) -> np.ndarray:
+    out = np.zeros(FPS_WORDS, np.uint64)
+    q = query166.encode() if isinstance(query166, str) else bytes(query166)
+    if len(q) != FPS_BITS:
+        raise FpsError(FPS_ERR_INVALID_ARG, "fps_pack_query: query must have 166 characters")
+    _check(_lib.fps_pack_query(q, out.ctypes.data), "fps_pack_query")
+    return out
+
+
+def fps_pack_text(text, flags: int = 0):
+    """Host-only parse of library text: (packed uint64[N, 3], cids int64[N])."""
+    buf = np.frombuffer(bytes(text), dtype=np.uint8)
+    ptr = buf.ctypes.data if buf.size else None
+    n = ctypes.c_size_t(0)
+    err = ctypes.c_size_t(0)
+    st = _lib.fps_pack_text(ptr, buf.size, flags, None, None, 0, ctypes.byref(n), ctypes.byref(err))
+    _check(st, "fps_pack_text", err.value)
+    packed = np.zeros((max(n.value, 1), FPS_WORDS), np.uint64)
+    cids = np.zeros(max(n.value, 1), np.int64)
+    st = _lib.fps_pack_text(ptr, buf.size, flags, packed.ctypes.data, cids.ctypes.data, n.value, ctypes.byref(n),
+                            ctypes.byref(err))
+    _check(st, "fps_pack_text", err.value)
+    return packed[: n.value], cids[: n.value]

@@ -1,0 +1,773 @@
+// Host side of the C ABI: library parsing/packing, popcount-bucketed layout,
+// device residency, per-stream workspaces and the search entry points.
+//
+// Paper: Fig. 3 step 1 ("obtain all the molecules from F, construct CID,
+// matrix A") becomes a one-time parse of the library text into packed
+// 24-byte records that stay in GPU memory; step 2 (the target's vector B)
+// becomes fps_pack_query; steps 3-6 run on the GPU (fps_scan.cu).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "fps_internal.h"
+
+using namespace fps;
+
+namespace {
+
+// ------------------------------------------------------------------ utilities
+int hw_threads() {
+  unsigned n = std::thread::hardware_concurrency();
+  return n ? static_cast<int>(std::min(n, 64u)) : 4;
+}
+
+template <class F>
+void parallel_for(int64_t n, int threads, F&& fn) {  // fn(t, lo, hi)
+  if (threads < 1) threads = 1;
+  if (n < 65536) threads = 1;
+  int64_t chunk = (n + threads - 1) / threads;
+  std::vector<std::thread> pool;
+  for (int t = 1; t < threads; ++t) {
+    int64_t lo = std::min<int64_t>(n, chunk * t), hi = std::min<int64_t>(n, lo + chunk);
+    pool.emplace_back([&fn, t, lo, hi] { fn(t, lo, hi); });
+  }
+  fn(0, 0, std::min<int64_t>(n, chunk));
+  for (auto& th : pool) th.join();
+}
+
+inline int popc3(const uint64_t* w) {
+  return __builtin_popcountll(w[0]) + __builtin_popcountll(w[1]) + __builtin_popcountll(w[2]);
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+// ---------------------------------------------------------------- text parse
+// One line (without '\n') -> packed record + CID.  Returns false on a format error.
+bool parse_line(const char* s, int64_t len, uint32_t flags, uint64_t w[3], int64_t* cid, bool* has_cid) {
+  if (len > 0 && s[len - 1] == '\r') --len;
+  const char* bits = nullptr;
+  *has_cid = false;
+  auto all01 = [](const char* p, int64_t n) {
+    for (int64_t j = 0; j < n; ++j)
+      if (p[j] != '0' && p[j] != '1') return false;
+    return true;
+  };
+  if (len == kBits && all01(s, len)) {
+    bits = s;
+  } else if (len == kBits + 1 && (flags & FPS_LOAD_ACCEPT_167) && s[0] == '0' && all01(s, len)) {
+    bits = s + 1;
+  } else {
+    int64_t sep = -1;
+    for (int64_t j = 0; j < len; ++j) {
+      char c = s[j];
+      if (c == ' ' || c == '\t' || c == ',') {
+        sep = j;
+        break;
+      }
+    }
+    if (sep <= 0 || len - sep - 1 != kBits || !all01(s + sep + 1, kBits)) return false;
+    int64_t v = 0;
+    for (int64_t j = 0; j < sep; ++j) {
+      char c = s[j];
+      if (c < '0' || c > '9' || v > (INT64_MAX - 9) / 10) return false;
+      v = v * 10 + (c - '0');
+    }
+    bits = s + sep + 1;
+    *cid = v;
+    *has_cid = true;
+  }
+  w[0] = w[1] = w[2] = 0;
+  for (int j = 0; j < kBits; ++j) w[j >> 6] |= static_cast<uint64_t>(bits[j] - '0') << (j & 63);
+  return true;
+}
+
+struct Parsed {
+  std::vector<uint64_t> packed;
+  std::vector<int64_t> cids;
+  bool any_cid = false;
+  int64_t n = 0;
+};
+
+// Multi-threaded parse: chunks split at line boundaries, counted, then filled in place.
+fps_status parse_text(const char* text, size_t len, uint32_t flags, Parsed* out, size_t* err_line) {
+  const int T = len < (1u << 20) ? 1 : hw_threads();
+  std::vector<size_t> cut(T + 1, len);
+  cut[0] = 0;
+  for (int t = 1; t < T; ++t) {
+    size_t p = len * static_cast<size_t>(t) / T;
+    while (p < len && text[p - 1] != '\n') ++p;
+    cut[t] = std::max(p, cut[t - 1]);
+  }
+  std::vector<int64_t> lines(T, 0);
+  auto count_lines = [&](int t) {
+    int64_t c = 0;
+    for (size_t p = cut[t]; p < cut[t + 1]; ++p) c += text[p] == '\n';
+    if (cut[t + 1] == len && len > cut[t] && text[len - 1] != '\n') c += 1;
+    lines[t] = c;
+  };
+  {
+    std::vector<std::thread> pool;
+    for (int t = 1; t < T; ++t) pool.emplace_back(count_lines, t);
+    count_lines(0);
+    for (auto& th : pool) th.join();
+  }
+  std::vector<int64_t> first(T + 1, 0);
+  for (int t = 0; t < T; ++t) first[t + 1] = first[t] + lines[t];
+  const int64_t n = first[T];
+  if (n >= (static_cast<int64_t>(1) << 31) - 1) return FPS_ERR_UNSUPPORTED;
+  try {
+    out->packed.assign(static_cast<size_t>(n) * 3, 0);
+    out->cids.assign(static_cast<size_t>(n), 0);
+  } catch (const std::bad_alloc&) {
+    return FPS_ERR_NOMEM;
+  }
+  std::vector<int64_t> bad(T, -1);
+  std::vector<char> saw_cid(T, 0);
+  auto fill = [&](int t) {
+    int64_t row = first[t];
+    size_t p = cut[t];
+    while (p < cut[t + 1]) {
+      size_t e = p;
+      while (e < len && text[e] != '\n') ++e;
+      int64_t cid = row;
+      bool hc = false;
+      if (!parse_line(text + p, static_cast<int64_t>(e - p), flags, &out->packed[3 * row], &cid, &hc)) {
+        bad[t] = row;
+        return;
+      }
+      out->cids[row] = cid;
+      saw_cid[t] |= hc;
+      ++row;
+      p = e + 1;
+    }
+  };
+  {
+    std::vector<std::thread> pool;
+    for (int t = 1; t < T; ++t) pool.emplace_back(fill, t);
+    fill(0);
+    for (auto& th : pool) th.join();
+  }
+  for (int t = 0; t < T; ++t) {
+    if (bad[t] >= 0) {
+      if (err_line) *err_line = static_cast<size_t>(bad[t] + 1);
+      return FPS_ERR_PARSE;
+    }
+    out->any_cid |= saw_cid[t] != 0;
+  }
+  out->n = n;
+  return FPS_OK;
+}
+
+// --------------------------------------------------------------- device alloc
+fps_status dev_alloc(Library* L, void** p, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (cudaMalloc(p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return FPS_ERR_CUDA;
+  }
+  L->allocations.push_back(*p);
+  L->device_bytes += bytes;
+  return FPS_OK;
+}
+
+void free_library(Library* L) {
+  if (!L) return;
+  DeviceGuard g(L->device);
+  for (auto& kv : L->ws) {
+    Workspace* w = kv.second;
+    if (w->block) cudaFree(w->block);
+    if (w->io_host) cudaFreeHost(w->io_host);
+    if (w->batch_block) cudaFree(w->batch_block);
+    if (w->batch_host) cudaFreeHost(w->batch_host);
+    delete w;
+  }
+  L->ws.clear();
+  for (void* p : L->allocations) cudaFree(p);
+  L->allocations.clear();
+  delete L;
+}
+
+// Bytes the resident layout needs on the device.
+struct Layout {
+  int64_t n_tiles = 0;
+  int64_t pos_base[kNumBuckets + 1] = {};
+  int64_t count[kNumBuckets] = {};
+  size_t bytes = 0;
+};
+
+Layout plan_layout(const uint64_t* packed, int64_t n, bool bucketed, std::vector<uint8_t>* popc) {
+  Layout lay;
+  if (bucketed) {
+    popc->resize(static_cast<size_t>(n));
+    const int T = hw_threads();
+    std::vector<std::vector<int64_t>> cnt(T, std::vector<int64_t>(kNumBuckets, 0));
+    parallel_for(n, T, [&](int t, int64_t lo, int64_t hi) {
+      for (int64_t i = lo; i < hi; ++i) {
+        int b = popc3(packed + 3 * i);
+        (*popc)[i] = static_cast<uint8_t>(b);
+        cnt[t][b] += 1;
+      }
+    });
+    for (auto& c : cnt)
+      for (int b = 0; b < kNumBuckets; ++b) lay.count[b] += c[b];
+    int64_t run = 0;
+    for (int b = 0; b < kNumBuckets; ++b) {
+      lay.pos_base[b] = run;
+      run += (lay.count[b] + kBucketAlign - 1) / kBucketAlign * kBucketAlign;
+    }
+    lay.pos_base[kNumBuckets] = run;
+    lay.n_tiles = run / kTile;
+  } else {
+    lay.count[0] = n;
+    lay.n_tiles = (n + kBucketAlign - 1) / kBucketAlign * (kBucketAlign / kTile);
+    lay.pos_base[0] = 0;
+    for (int b = 1; b <= kNumBuckets; ++b) lay.pos_base[b] = lay.n_tiles * kTile;
+  }
+  lay.bytes = static_cast<size_t>(lay.n_tiles) * kTileBytes + static_cast<size_t>(lay.n_tiles) * kTile * 4 +
+              2 * (kNumBuckets + 1) * sizeof(int32_t);
+  return lay;
+}
+
+fps_status build_library(const uint64_t* packed, int64_t n, const int64_t* cids, const fps_load_desc* d,
+                         Library** out) {
+  for (int64_t i = 0; i < n; ++i)
+    if (packed[3 * i + 2] >> (kBits - 128)) return FPS_ERR_INVALID_ARG;  // pad bits must be zero
+  const bool bucketed = !(d->flags & FPS_LOAD_NO_BUCKETS);
+  std::vector<uint8_t> popc;
+  Layout lay = plan_layout(packed, n, bucketed, &popc);
+  size_t need = lay.bytes;
+  if (d->hbm_budget_bytes && need > d->hbm_budget_bytes) return FPS_ERR_BUDGET;
+
+  Library* L = new (std::nothrow) Library();
+  if (!L) return FPS_ERR_NOMEM;
+  L->device = d->device;
+  L->n = n;
+  L->n_tiles = lay.n_tiles;
+  L->bucketed = bucketed ? 1 : 0;
+  if (cids) L->cids.assign(cids, cids + n);
+  for (int b = 0; b < kNumBuckets; ++b) L->bucket_count[b] = bucketed ? lay.count[b] : 0;
+
+  DeviceGuard g(d->device);
+  if (!g.ok) {
+    delete L;
+    return FPS_ERR_CUDA;
+  }
+  if (cudaDeviceGetAttribute(&L->num_sms, cudaDevAttrMultiProcessorCount, d->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete L;
+    return FPS_ERR_CUDA;
+  }
+
+  // host staging of the tiled layout
+  std::vector<uint64_t> words;
+  std::vector<int32_t> perm;
+  try {
+    words.assign(static_cast<size_t>(lay.n_tiles) * kTile * kWords, 0);
+    perm.assign(static_cast<size_t>(lay.n_tiles) * kTile, -1);
+  } catch (const std::bad_alloc&) {
+    delete L;
+    return FPS_ERR_NOMEM;
+  }
+  auto place = [&](int64_t i, int64_t p) {
+    int64_t t = p / kTile, r = p % kTile;
+    uint64_t* base = &words[static_cast<size_t>(t) * kTile * kWords];
+    base[r] = packed[3 * i];
+    base[kTile + r] = packed[3 * i + 1];
+    base[2 * kTile + r] = packed[3 * i + 2];
+    perm[p] = static_cast<int32_t>(i);
+  };
+  const int T = hw_threads();
+  if (bucketed) {
+    // stable counting sort by popcount: per-thread offsets keep index order inside a bucket
+    // parallel_for hands thread t the same index range in both passes
+    std::vector<std::vector<int64_t>> cnt(T, std::vector<int64_t>(kNumBuckets, 0));
+    parallel_for(n, T, [&](int t, int64_t lo, int64_t hi) {
+      for (int64_t i = lo; i < hi; ++i) cnt[t][popc[i]] += 1;
+    });
+    std::vector<std::vector<int64_t>> off(T, std::vector<int64_t>(kNumBuckets, 0));
+    for (int b = 0; b < kNumBuckets; ++b) {
+      int64_t run = lay.pos_base[b];
+      for (int t = 0; t < T; ++t) {
+        off[t][b] = run;
+        run += cnt[t][b];
+      }
+    }
+    parallel_for(n, T, [&](int t, int64_t lo, int64_t hi) {
+      for (int64_t i = lo; i < hi; ++i) place(i, off[t][popc[i]]++);
+    });
+  } else {
+    parallel_for(n, T, [&](int, int64_t lo, int64_t hi) {
+      for (int64_t i = lo; i < hi; ++i) place(i, i);
+    });
+  }
+  std::vector<int32_t> tile_off(kNumBuckets + 1, 0), bcount(kNumBuckets + 1, 0);
+  for (int b = 0; b <= kNumBuckets; ++b) tile_off[b] = static_cast<int32_t>(lay.pos_base[b] / kTile);
+  for (int b = 0; b < kNumBuckets; ++b) bcount[b] = static_cast<int32_t>(lay.count[b]);
+
+  void *dw = nullptr, *dp = nullptr, *dto = nullptr, *dbc = nullptr;
+  fps_status st = dev_alloc(L, &dw, words.size() * 8);
+  if (st == FPS_OK) st = dev_alloc(L, &dp, perm.size() * 4);
+  if (st == FPS_OK) st = dev_alloc(L, &dto, tile_off.size() * 4);
+  if (st == FPS_OK) st = dev_alloc(L, &dbc, bcount.size() * 4);
+  if (st == FPS_OK) {
+    if (cudaMemcpy(dw, words.data(), words.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(dp, perm.data(), perm.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(dto, tile_off.data(), tile_off.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(dbc, bcount.data(), bcount.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaGetLastError();
+      st = FPS_ERR_CUDA;
+    }
+  }
+  if (st != FPS_OK) {
+    free_library(L);
+    return st;
+  }
+  L->dev.words = static_cast<const uint64_t*>(dw);
+  L->dev.perm = static_cast<const int32_t*>(dp);
+  L->dev.tile_off = static_cast<const int32_t*>(dto);
+  L->dev.bcount = static_cast<const int32_t*>(dbc);
+  L->dev.n = n;
+  L->dev.n_tiles = lay.n_tiles;
+  L->dev.bucketed = L->bucketed;
+  *out = L;
+  return FPS_OK;
+}
+
+// ------------------------------------------------------------------ workspaces
+fps_status get_workspace(Library* L, cudaStream_t s, Workspace** out) {
+  std::lock_guard<std::mutex> lock(L->mu);
+  auto it = L->ws.find(s);
+  if (it != L->ws.end()) {
+    *out = it->second;
+    return FPS_OK;
+  }
+  Workspace* w = new (std::nothrow) Workspace();
+  if (!w) return FPS_ERR_NOMEM;
+  w->cand_cap = scan_cand_capacity(L->num_sms);
+  size_t st_bytes = (sizeof(ScanState) + 255) / 256 * 256;
+  size_t io_bytes = (sizeof(HostIO) + 255) / 256 * 256;
+  size_t bytes = st_bytes + io_bytes + w->cand_cap * sizeof(unsigned long long);
+  if (cudaMalloc(&w->block, bytes) != cudaSuccess || cudaMallocHost(&w->io_host, sizeof(HostIO)) != cudaSuccess) {
+    cudaGetLastError();
+    if (w->block) cudaFree(w->block);
+    delete w;
+    return FPS_ERR_CUDA;
+  }
+  char* b = static_cast<char*>(w->block);
+  w->st = reinterpret_cast<ScanState*>(b);
+  w->io = reinterpret_cast<HostIO*>(b + st_bytes);
+  w->cand = reinterpret_cast<unsigned long long*>(b + st_bytes + io_bytes);
+  if (cudaMemsetAsync(w->io, 0, sizeof(HostIO), s) != cudaSuccess || scan_state_init(w->st, s) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(w->block);
+    cudaFreeHost(w->io_host);
+    delete w;
+    return FPS_ERR_CUDA;
+  }
+  L->ws[s] = w;
+  *out = w;
+  return FPS_OK;
+}
+
+fps_status check_k(int k) {
+  if (k < 0) return FPS_ERR_INVALID_ARG;
+  if (k > kKMax) return FPS_ERR_UNSUPPORTED;
+  return FPS_OK;
+}
+
+// Read and clear the device error word of a workspace (stream already synchronised).
+fps_status take_device_error(Workspace* w, cudaStream_t s) {
+  uint32_t e = 0;
+  if (cudaMemcpyAsync(&e, &w->io->err, sizeof e, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaGetLastError();
+    return FPS_ERR_CUDA;
+  }
+  if (!e) return FPS_OK;
+  // a failed scan may leave its state dirty: clear error word and scan state
+  if (cudaMemsetAsync(&w->io->err, 0, sizeof(uint32_t), s) != cudaSuccess || scan_state_init(w->st, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaGetLastError();
+    return FPS_ERR_CUDA;
+  }
+  if (e & DEVERR_TIMEOUT) return FPS_ERR_TIMEOUT;
+  return FPS_ERR_OVERFLOW_INTERNAL;
+}
+
+double opt_timeout(const fps_search_opts* o) { return (o && o->timeout_s > 0) ? o->timeout_s : 2.0; }
+
+// Host-IO single search through the workspace staging buffers.
+fps_status search_one_host(Library* L, const uint64_t q[3], int k, int32_t* out_index, int32_t* out_dist,
+                           int32_t* out_count, const fps_search_opts* opts, cudaStream_t s) {
+  if (L->n == 0 || k == 0) {
+    *out_count = 0;
+    return FPS_OK;
+  }
+  Workspace* w = nullptr;
+  fps_status st = get_workspace(L, s, &w);
+  if (st != FPS_OK) return st;
+  std::memcpy(w->io_host->query, q, 3 * sizeof(uint64_t));
+  const int k_eff = static_cast<int>(std::min<int64_t>(k, L->n));
+  if (cudaMemcpyAsync(w->io->query, w->io_host->query, 4 * sizeof(uint64_t), cudaMemcpyHostToDevice, s) != cudaSuccess) {
+    cudaGetLastError();
+    return FPS_ERR_CUDA;
+  }
+  if (launch_scan_single(L->dev, w->io->query, k, w->st, w->cand, w->io->res, w->io->res + k_eff, &w->io->count,
+                         &w->io->err, L->num_sms, opt_timeout(opts), s) != cudaSuccess) {
+    cudaGetLastError();
+    return FPS_ERR_CUDA;
+  }
+  size_t bytes = offsetof(HostIO, res) - offsetof(HostIO, err) + 2 * sizeof(int32_t) * k_eff;
+  if (cudaMemcpyAsync(&w->io_host->err, &w->io->err, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaGetLastError();
+    return FPS_ERR_CUDA;
+  }
+  if (w->io_host->err) return take_device_error(w, s);
+  const int c = w->io_host->count;
+  std::memcpy(out_index, w->io_host->res, sizeof(int32_t) * c);
+  std::memcpy(out_dist, w->io_host->res + k_eff, sizeof(int32_t) * c);
+  *out_count = c;
+  if (opts && opts->stats) {
+    opts->stats->queries = 1;
+    opts->stats->fallbacks = 0;
+    opts->stats->candidates = 0;
+    opts->stats->path_used = FPS_PATH_POPC;
+  }
+  return FPS_OK;
+}
+
+
+// Grow the per-stream batch staging (device block and pinned host block).
+fps_status batch_staging(Workspace* w, size_t dev_bytes, size_t host_bytes) {
+  if (w->batch_bytes < dev_bytes) {
+    if (w->batch_block) cudaFree(w->batch_block);
+    w->batch_block = nullptr;
+    w->batch_bytes = 0;
+    if (cudaMalloc(&w->batch_block, dev_bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return FPS_ERR_CUDA;
+    }
+    w->batch_bytes = dev_bytes;
+  }
+  if (w->batch_host_bytes < host_bytes) {
+    if (w->batch_host) cudaFreeHost(w->batch_host);
+    w->batch_host = nullptr;
+    w->batch_host_bytes = 0;
+    if (cudaMallocHost(&w->batch_host, host_bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return FPS_ERR_CUDA;
+    }
+    w->batch_host_bytes = host_bytes;
+  }
+  return FPS_OK;
+}
+
+// Queries one after another through the single-query kernel (FPS_PATH_POPC).
+fps_status batch_sequential(Library* L, Workspace* w, const uint64_t* dq, int Q, const int32_t* k, const int64_t* off,
+                            int32_t* di, int32_t* dd, int32_t* dc, double tmo, cudaStream_t s) {
+  for (int q = 0; q < Q; ++q) {
+    if (k[q] == 0 || L->n == 0) {
+      if (cudaMemsetAsync(dc + q, 0, sizeof(int32_t), s) != cudaSuccess) {
+        cudaGetLastError();
+        return FPS_ERR_CUDA;
+      }
+      continue;
+    }
+    if (launch_scan_single(L->dev, dq + 3 * q, k[q], w->st, w->cand, di + off[q], dd + off[q], dc + q, &w->io->err,
+                           L->num_sms, tmo, s) != cudaSuccess) {
+      cudaGetLastError();
+      return FPS_ERR_CUDA;
+    }
+  }
+  return FPS_OK;
+}
+
+fps_status search_batch_impl(Library* L, const uint64_t* queries, int Q, const int32_t* k, const int64_t* off,
+                             int64_t total, int32_t* out_index, int32_t* out_dist, int32_t* out_count,
+                             const fps_search_opts* opts, bool dev_io, cudaStream_t s) {
+  if (Q == 0) return FPS_OK;
+  Workspace* w = nullptr;
+  fps_status st = get_workspace(L, s, &w);
+  if (st != FPS_OK) return st;
+  const double tmo = opt_timeout(opts);
+  if (dev_io) return batch_sequential(L, w, queries, Q, k, off, out_index, out_dist, out_count, tmo, s);
+  for (int q = 0; q < Q; ++q)
+    if (queries[3 * q + 2] >> (kBits - 128)) return FPS_ERR_INVALID_ARG;
+  // device staging: [queries Q*3][index total][dist total][count Q]; host mirror of the same
+  const size_t qb = static_cast<size_t>(Q) * 3 * sizeof(uint64_t);
+  const size_t rb = static_cast<size_t>(total) * sizeof(int32_t);
+  const size_t cb = static_cast<size_t>(Q) * sizeof(int32_t);
+  const size_t bytes = qb + 2 * rb + cb;
+  st = batch_staging(w, bytes, bytes);
+  if (st != FPS_OK) return st;
+  char* hb = static_cast<char*>(w->batch_host);
+  char* db = static_cast<char*>(w->batch_block);
+  std::memcpy(hb, queries, qb);
+  if (cudaMemcpyAsync(db, hb, qb, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+    cudaGetLastError();
+    return FPS_ERR_CUDA;
+  }
+  int32_t* di = reinterpret_cast<int32_t*>(db + qb);
+  int32_t* dd = reinterpret_cast<int32_t*>(db + qb + rb);
+  int32_t* dc = reinterpret_cast<int32_t*>(db + qb + 2 * rb);
+  st = batch_sequential(L, w, reinterpret_cast<const uint64_t*>(db), Q, k, off, di, dd, dc, tmo, s);
+  if (st != FPS_OK) return st;
+  if (cudaMemcpyAsync(hb + qb, db + qb, 2 * rb + cb, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaGetLastError();
+    return FPS_ERR_CUDA;
+  }
+  st = take_device_error(w, s);
+  if (st != FPS_OK) return st;
+  const int32_t* hi = reinterpret_cast<const int32_t*>(hb + qb);
+  const int32_t* hd = reinterpret_cast<const int32_t*>(hb + qb + rb);
+  const int32_t* hc = reinterpret_cast<const int32_t*>(hb + qb + 2 * rb);
+  for (int q = 0; q < Q; ++q) {
+    out_count[q] = hc[q];
+    std::memcpy(out_index + off[q], hi + off[q], sizeof(int32_t) * hc[q]);
+    std::memcpy(out_dist + off[q], hd + off[q], sizeof(int32_t) * hc[q]);
+  }
+  if (opts && opts->stats) {
+    opts->stats->queries = Q;
+    opts->stats->fallbacks = 0;
+    opts->stats->candidates = 0;
+    opts->stats->path_used = FPS_PATH_POPC;
+  }
+  return FPS_OK;
+}
+
+}  // namespace
+
+// ===================================================================== C ABI
+extern "C" {
+
+const char* fps_status_string(fps_status st) {
+  switch (st) {
+    case FPS_OK: return "ok";
+    case FPS_ERR_INVALID_ARG: return "invalid argument";
+    case FPS_ERR_IO: return "cannot read library file";
+    case FPS_ERR_PARSE: return "malformed library line";
+    case FPS_ERR_BUDGET: return "library exceeds the device memory budget";
+    case FPS_ERR_CUDA: return "CUDA runtime error";
+    case FPS_ERR_TIMEOUT: return "device-side wait timed out";
+    case FPS_ERR_OVERFLOW_INTERNAL: return "internal candidate buffer overflow";
+    case FPS_ERR_UNSUPPORTED: return "unsupported request";
+    case FPS_ERR_NOMEM: return "host out of memory";
+  }
+  return "unknown status";
+}
+
+fps_status fps_pack_query(const char* query166, uint64_t out[FPS_WORDS]) {
+  if (!query166 || !out) return FPS_ERR_INVALID_ARG;
+  uint64_t w[3] = {0, 0, 0};
+  for (int j = 0; j < kBits; ++j) {
+    char c = query166[j];
+    if (c != '0' && c != '1') return FPS_ERR_INVALID_ARG;
+    w[j >> 6] |= static_cast<uint64_t>(c - '0') << (j & 63);
+  }
+  out[0] = w[0];
+  out[1] = w[1];
+  out[2] = w[2];
+  return FPS_OK;
+}
+
+fps_status fps_pack_text(const char* text, size_t text_len, uint32_t flags, uint64_t* out_packed, int64_t* out_cids,
+                         size_t cap, size_t* out_n, size_t* err_line) {
+  if ((!text && text_len) || !out_n) return FPS_ERR_INVALID_ARG;
+  Parsed p;
+  fps_status st = parse_text(text ? text : "", text_len, flags, &p, err_line);
+  if (st != FPS_OK) return st;
+  *out_n = static_cast<size_t>(p.n);
+  if (!out_packed) return FPS_OK;
+  if (static_cast<size_t>(p.n) > cap) return FPS_ERR_INVALID_ARG;
+  std::memcpy(out_packed, p.packed.data(), p.packed.size() * sizeof(uint64_t));
+  if (out_cids) std::memcpy(out_cids, p.cids.data(), p.cids.size() * sizeof(int64_t));
+  return FPS_OK;
+}
+
+fps_status fps_library_load(const fps_load_desc* d, fps_library* out) {
+  if (!d || !out) return FPS_ERR_INVALID_ARG;
+  *out = nullptr;
+  int sources = (d->path != nullptr) + (d->text != nullptr) + (d->packed != nullptr);
+  if (sources != 1) return FPS_ERR_INVALID_ARG;
+  Library* L = nullptr;
+  fps_status st;
+  if (d->packed) {
+    if (d->n_packed >= (static_cast<size_t>(1) << 31) - 1) return FPS_ERR_UNSUPPORTED;
+    st = build_library(d->packed, static_cast<int64_t>(d->n_packed), d->cids, d, &L);
+  } else {
+    std::vector<char> file;
+    const char* text = d->text;
+    size_t len = d->text_len;
+    if (d->path) {
+      FILE* f = std::fopen(d->path, "rb");
+      if (!f) return FPS_ERR_IO;
+      std::fseek(f, 0, SEEK_END);
+      long sz = std::ftell(f);
+      std::fseek(f, 0, SEEK_SET);
+      if (sz < 0) {
+        std::fclose(f);
+        return FPS_ERR_IO;
+      }
+      try {
+        file.resize(static_cast<size_t>(sz));
+      } catch (const std::bad_alloc&) {
+        std::fclose(f);
+        return FPS_ERR_NOMEM;
+      }
+      size_t got = sz ? std::fread(file.data(), 1, file.size(), f) : 0;
+      std::fclose(f);
+      if (got != file.size()) return FPS_ERR_IO;
+      text = file.data();
+      len = file.size();
+    }
+    Parsed p;
+    st = parse_text(text ? text : "", len, d->flags, &p, d->err_line);
+    if (st != FPS_OK) return st;
+    st = build_library(p.packed.data(), p.n, p.any_cid ? p.cids.data() : nullptr, d, &L);
+  }
+  if (st == FPS_OK) *out = reinterpret_cast<fps_library>(L);
+  return st;
+}
+
+fps_status fps_release(fps_library lib) {
+  if (!lib) return FPS_OK;
+  Library* L = reinterpret_cast<Library*>(lib);
+  free_library(L);
+  return FPS_OK;
+}
+
+fps_status fps_library_info_get(fps_library lib, fps_library_info* info) {
+  if (!lib || !info) return FPS_ERR_INVALID_ARG;
+  Library* L = reinterpret_cast<Library*>(lib);
+  std::memset(info, 0, sizeof *info);
+  info->n_records = L->n;
+  info->n_tiles = L->n_tiles;
+  info->device_bytes = L->device_bytes;
+  info->device = L->device;
+  info->bucketed = L->bucketed;
+  info->has_tc_operand = 0;
+  for (int b = 0; b < kNumBuckets; ++b) info->bucket_count[b] = L->bucket_count[b];
+  return FPS_OK;
+}
+
+fps_status fps_library_cid(fps_library lib, int64_t index, int64_t* cid) {
+  if (!lib || !cid) return FPS_ERR_INVALID_ARG;
+  Library* L = reinterpret_cast<Library*>(lib);
+  if (index < 0 || index >= L->n) return FPS_ERR_INVALID_ARG;
+  *cid = L->cids.empty() ? index : L->cids[static_cast<size_t>(index)];
+  return FPS_OK;
+}
+
+fps_status fps_search(fps_library lib, const char* query166, int k, int32_t* out_index, int32_t* out_dist,
+                      int64_t* out_cid, int* out_count, void* cuda_stream) {
+  if (!lib || !query166 || !out_count || (k > 0 && (!out_index || !out_dist))) return FPS_ERR_INVALID_ARG;
+  fps_status st = check_k(k);
+  if (st != FPS_OK) return st;
+  uint64_t q[3];
+  st = fps_pack_query(query166, q);
+  if (st != FPS_OK) return st;
+  Library* L = reinterpret_cast<Library*>(lib);
+  DeviceGuard g(L->device);
+  if (!g.ok) return FPS_ERR_CUDA;
+  int32_t c = 0;
+  st = search_one_host(L, q, k, out_index, out_dist, &c, nullptr, static_cast<cudaStream_t>(cuda_stream));
+  if (st != FPS_OK) return st;
+  if (out_cid)
+    for (int i = 0; i < c; ++i) out_cid[i] = L->cids.empty() ? out_index[i] : L->cids[out_index[i]];
+  *out_count = c;
+  return FPS_OK;
+}
+
+fps_status fps_search_packed(fps_library lib, const uint64_t* query, int k, int32_t* out_index, int32_t* out_dist,
+                             int32_t* out_count, const fps_search_opts* opts, void* cuda_stream) {
+  if (!lib || !query || !out_count || (k > 0 && (!out_index || !out_dist))) return FPS_ERR_INVALID_ARG;
+  fps_status st = check_k(k);
+  if (st != FPS_OK) return st;
+  Library* L = reinterpret_cast<Library*>(lib);
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  DeviceGuard g(L->device);
+  if (!g.ok) return FPS_ERR_CUDA;
+  const bool dev_io = opts && (opts->flags & FPS_SEARCH_DEVICE_IO);
+  if (!dev_io) {
+    if (query[2] >> (kBits - 128)) return FPS_ERR_INVALID_ARG;
+    return search_one_host(L, query, k, out_index, out_dist, out_count, opts, s);
+  }
+  if (L->n == 0 || k == 0) {
+    if (cudaMemsetAsync(out_count, 0, sizeof(int32_t), s) != cudaSuccess) {
+      cudaGetLastError();
+      return FPS_ERR_CUDA;
+    }
+    return FPS_OK;
+  }
+  Workspace* w = nullptr;
+  st = get_workspace(L, s, &w);
+  if (st != FPS_OK) return st;
+  if (launch_scan_single(L->dev, query, k, w->st, w->cand, out_index, out_dist, out_count, &w->io->err, L->num_sms,
+                         opt_timeout(opts), s) != cudaSuccess) {
+    cudaGetLastError();
+    return FPS_ERR_CUDA;
+  }
+  return FPS_OK;
+}
+
+
+fps_status fps_search_batch(fps_library lib, const uint64_t* queries, int Q, const int32_t* k,
+                            const int64_t* out_offsets, int32_t* out_index, int32_t* out_dist, int32_t* out_count,
+                            const fps_search_opts* opts, void* cuda_stream) {
+  if (!lib || Q < 0 || (Q > 0 && (!queries || !k || !out_offsets || !out_index || !out_dist || !out_count)))
+    return FPS_ERR_INVALID_ARG;
+  int64_t total = 0;
+  for (int q = 0; q < Q; ++q) {
+    fps_status st = check_k(k[q]);
+    if (st != FPS_OK) return st;
+    if (out_offsets[q] < 0 || out_offsets[q + 1] - out_offsets[q] < k[q]) return FPS_ERR_INVALID_ARG;
+    total = std::max<int64_t>(total, out_offsets[q + 1]);
+  }
+  Library* L = reinterpret_cast<Library*>(lib);
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  DeviceGuard g(L->device);
+  if (!g.ok) return FPS_ERR_CUDA;
+  const bool dev_io = opts && (opts->flags & FPS_SEARCH_DEVICE_IO);
+  return search_batch_impl(L, queries, Q, k, out_offsets, total, out_index, out_dist, out_count, opts, dev_io, s);
+}
+
+fps_status fps_sync(fps_library lib, void* cuda_stream) {
+  if (!lib) return FPS_ERR_INVALID_ARG;
+  Library* L = reinterpret_cast<Library*>(lib);
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  DeviceGuard g(L->device);
+  if (!g.ok) return FPS_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaGetLastError();
+    return FPS_ERR_CUDA;
+  }
+  Workspace* w = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(L->mu);
+    auto it = L->ws.find(s);
+    if (it == L->ws.end()) return FPS_OK;
+    w = it->second;
+  }
+  return take_device_error(w, s);
+}
+
+}  // extern "C"

@@ -1,0 +1,110 @@
+// Internal declarations shared by the host library code and the CUDA kernels.
+// Nothing here crosses the C ABI (include/fps.h is the public boundary).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <map>
+#include <mutex>
+#include <vector>
+
+#include "fps.h"
+
+namespace fps {
+
+constexpr int kBits = FPS_BITS;        // 166 MACCS keys (Sec. 4.2)
+constexpr int kWords = FPS_WORDS;      // 3 x uint64 per record
+constexpr int kTile = 128;             // records per scan tile: [3][128] uint64 = 3 KB contiguous
+constexpr int kTileBytes = kTile * kWords * 8;
+constexpr int kBucketAlign = 256;      // every popcount bucket starts on a 256-record boundary
+constexpr int kNumBuckets = kBits + 1; // popcounts 0..166
+constexpr int kKMax = FPS_K_MAX;
+
+// Device view of a resident library, passed to kernels by value.
+//   words:    [n_tiles][3][kTile] uint64, word-major inside a tile, so a warp's
+//             loads of one word of 32 consecutive records are one 256-byte line;
+//   perm:     [n_tiles * kTile] original 0-based index of each position (-1 = pad);
+//   tile_off: [kNumBuckets + 1] first tile of each popcount bucket (bucket b holds
+//             the records with popc == b in ascending index, tiles tile_off[b]..);
+//   bcount:   [kNumBuckets] records per bucket.
+// Without buckets, bucket 0 holds every record in index order and pruning is off.
+struct DevLib {
+  const uint64_t* words;
+  const int32_t* perm;
+  const int32_t* tile_off;
+  const int32_t* bcount;
+  int64_t n;
+  int64_t n_tiles;
+  int bucketed;
+};
+
+// Running state of one single-query scan.  Lives at the start of a per-stream
+// workspace; the last block of every scan restores it to the initial values, so
+// consecutive scans on one stream need no memset.
+struct ScanState {
+  uint32_t hist[168];            // accepted records per distance (distinct records)
+  unsigned long long thr_key;    // upper bound on the k-th key (d << 32 | index)
+  uint32_t thr_d;                // upper bound on the k-th distance
+  uint32_t done;                 // blocks finished
+  uint32_t ncand;                // keys written to the candidate array
+  uint32_t pad[5];
+};
+
+// Per-stream staging for host-IO searches; device copy and pinned host copy
+// share the layout so one copy moves each direction.
+struct HostIO {
+  uint64_t query[4];             // packed query (3 words used)
+  uint32_t err;                  // device error bits (FPS_DEVERR_*)
+  int32_t count;                 // results written
+  int32_t res[2 * kKMax];        // [index k][distance k]
+};
+
+enum : uint32_t { DEVERR_TIMEOUT = 1u, DEVERR_INTERNAL = 2u, DEVERR_OVERFLOW = 4u };
+
+struct Workspace {
+  ScanState* st = nullptr;       // device
+  HostIO* io = nullptr;          // device
+  HostIO* io_host = nullptr;     // pinned host
+  unsigned long long* cand = nullptr;
+  size_t cand_cap = 0;
+  void* block = nullptr;         // the one device allocation holding st, io and cand
+  // batched-path scratch (grown on demand)
+  void* batch_block = nullptr;
+  size_t batch_bytes = 0;
+  void* batch_host = nullptr;
+  size_t batch_host_bytes = 0;
+};
+
+struct Library {
+  int device = 0;
+  DevLib dev{};
+  std::vector<void*> allocations;
+  size_t device_bytes = 0;
+  int64_t n = 0;
+  int64_t n_tiles = 0;
+  int bucketed = 1;
+  std::vector<int64_t> cids;     // empty = CID is the index
+  int64_t bucket_count[kNumBuckets] = {};
+  int num_sms = 0;
+  std::mutex mu;
+  std::map<cudaStream_t, Workspace*> ws;
+};
+
+// ---- kernels (fps_scan.cu)
+// Scan configuration chosen for a given k.
+struct ScanConfig {
+  int warps;
+  int cap;
+  int kmax;
+  size_t smem;
+};
+ScanConfig scan_config_for(int k);
+size_t scan_cand_capacity(int num_sms);  // keys needed by the largest configuration
+cudaError_t scan_state_init(ScanState* st, cudaStream_t s);
+cudaError_t launch_scan_single(const DevLib& lib, const uint64_t* d_query, int k, ScanState* st,
+                               unsigned long long* cand, int32_t* out_idx, int32_t* out_dist, int32_t* out_count,
+                               uint32_t* err, int num_sms, double timeout_s, cudaStream_t s);
+
+}  // namespace fps

@@ -1,0 +1,663 @@
+// Single-query exhaustive scan + exact top-k (one launch per query).
+//
+// Paper: Sec. 4.3 (Manhattan distance over the 166 keys) and Fig. 3 (pair
+// each row with its distance, sort ascending, take the first k).  For 0/1 keys
+// |a_j - b_j| = a_j XOR b_j, so a row's distance is
+//   d = popc(q0 ^ x0) + popc(q1 ^ x1) + popc(q2 ^ x2)
+// over the three packed 64-bit words.  The top-k is the k smallest keys
+// key = d << 32 | index, i.e. ascending distance with ties by index.
+//
+// Design (one persistent CTA per SM, every warp independent):
+//   * each warp streams 3 KB tiles of the library through its own ring of
+//     shared-memory stages filled by 1-D TMA bulk copies (cp.async.bulk) that
+//     complete on per-stage mbarriers; the library is read once, evict-first;
+//   * tiles are visited by popcount bucket in order of the lower bound
+//     |popc q - popc x| <= d (nearest buckets first), and a warp stops as soon
+//     as the bound of its next tile exceeds the current distance threshold;
+//   * a record is a candidate iff its key is <= the running threshold key.
+//     The threshold is the min of (a) the smallest D such that at least k
+//     accepted records have d <= D, read from a global histogram of accepted
+//     distances, and (b) the k-th key of any warp's local buffer (atomicMin).
+//     Both are valid upper bounds of the true k-th key, so no top-k member is
+//     ever rejected;
+//   * candidates go to a per-warp shared buffer; a full buffer is filtered
+//     against the threshold and, if still longer than k, sorted and cut to k;
+//   * the last CTA to finish reads the histogram -- exact below the final
+//     threshold -- to get the k-th distance T and the number of records closer
+//     than T, keeps every candidate below T plus the smallest indices at T,
+//     sorts them and writes the result.  It then restores the scan state.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "fps_internal.h"
+
+namespace fps {
+namespace {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+constexpr int kStages = 3;
+constexpr int kTieCap = 16384;          // tie keys sorted in shared memory by the merge
+constexpr int kFinCap = 2048;           // >= FPS_K_MAX, power of two
+
+// ------------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Spin on an mbarrier phase, giving up at the deadline (no unbounded waits).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t deadline) {
+  while (!mbar_try_wait(bar, parity)) {
+    if (global_ns() > deadline) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ uint64_t l2_evict_first_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
+                                              uint64_t pol) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::
+          "r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(pol)
+      : "memory");
+}
+
+__device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void red_add_u32(uint32_t* p, uint32_t v) {
+  asm volatile("red.relaxed.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+__device__ __forceinline__ unsigned long long key_bound_of_dist(uint32_t d) {
+  return (static_cast<unsigned long long>(d) << 32) | 0xFFFFFFFFull;
+}
+
+// -------------------------------------------------------------- sorting helpers
+// Ascending bitonic sort of n (power of two) keys in shared memory by one warp.
+__device__ void warp_bitonic_sort(unsigned long long* s, int n, int lane) {
+  for (int kk = 2; kk <= n; kk <<= 1) {
+    for (int j = kk >> 1; j > 0; j >>= 1) {
+      for (int i = lane; i < (n >> 1); i += 32) {
+        int pos = 2 * i - (i & (j - 1));
+        int par = pos + j;
+        bool asc = (pos & kk) == 0;
+        unsigned long long a = s[pos], b = s[par];
+        if ((a > b) == asc) {
+          s[pos] = b;
+          s[par] = a;
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
+// Same, by the whole block.
+__device__ void block_bitonic_sort(unsigned long long* s, int n) {
+  for (int kk = 2; kk <= n; kk <<= 1) {
+    for (int j = kk >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < (n >> 1); i += blockDim.x) {
+        int pos = 2 * i - (i & (j - 1));
+        int par = pos + j;
+        bool asc = (pos & kk) == 0;
+        unsigned long long a = s[pos], b = s[par];
+        if ((a > b) == asc) {
+          s[pos] = b;
+          s[par] = a;
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+__device__ __forceinline__ int next_pow2(int v) {
+  int p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+// ---------------------------------------------------------- per-warp candidates
+// Drop keys above the threshold; if more than k remain, sort and keep k, and
+// publish the k-th key as a global bound.  Returns the new count.
+__device__ int compact_buffer(unsigned long long* buf, int cnt, int k, unsigned long long& thr_key,
+                              ScanState* st, int lane) {
+  int kept = 0;
+  for (int base = 0; base < cnt; base += 32) {
+    int i = base + lane;
+    unsigned long long v = i < cnt ? buf[i] : ~0ull;
+    bool keep = i < cnt && v <= thr_key;
+    __syncwarp();
+    uint32_t bal = __ballot_sync(kFull, keep);
+    if (keep) buf[kept + __popc(bal & lanemask_lt())] = v;
+    kept += __popc(bal);
+  }
+  __syncwarp();
+  if (kept > k) {
+    int p = next_pow2(kept);
+    for (int i = kept + lane; i < p; i += 32) buf[i] = ~0ull;
+    __syncwarp();
+    warp_bitonic_sort(buf, p, lane);
+    kept = k;
+    unsigned long long kth = buf[k - 1];
+    if (kth < thr_key) {
+      thr_key = kth;
+      if (lane == 0) atomicMin(&st->thr_key, kth);
+    }
+  }
+  __syncwarp();
+  return kept;
+}
+
+// The smallest D with at least k accepted records at distance <= D; 167 if none.
+__device__ uint32_t bound_from_hist(const ScanState* st, int k, int lane) {
+  uint32_t carry = 0;
+  uint32_t found = 167;
+  for (int c = 0; c < 6; ++c) {
+    int b = c * 32 + lane;
+    uint32_t v = b < kNumBuckets ? ld_relaxed_u32(&st->hist[b]) : 0u;
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t t = __shfl_up_sync(kFull, v, o);
+      if (lane >= o) v += t;
+    }
+    v += carry;
+    uint32_t bal = __ballot_sync(kFull, v >= static_cast<uint32_t>(k));
+    if (bal && found == 167) found = c * 32 + __ffs(bal) - 1;
+    carry = __shfl_sync(kFull, v, 31);
+  }
+  return found;
+}
+
+struct Tables {
+  int lv_start[kNumBuckets + 2];  // items before level L (level = |popc q - bucket|)
+  int lo_b[kNumBuckets + 1];      // bucket popc q - L, or -1
+  int hi_b[kNumBuckets + 1];      // bucket popc q + L, or -1
+  int nt_lo[kNumBuckets + 1];     // tiles holding records in lo_b
+  int tile_off[kNumBuckets + 1];
+  int bcount[kNumBuckets + 1];
+  int nlev;
+  int is_last;
+  int nfin;
+  int ntie;
+  int T;
+  int cless;
+};
+
+struct Item {
+  int64_t tile;
+  int level;
+  int nvalid;
+};
+
+__device__ __forceinline__ int tiles_of(int count) { return (count + kTile - 1) / kTile; }
+
+__device__ __forceinline__ Item locate(const Tables& tb, int t, int& cur) {
+  while (t >= tb.lv_start[cur + 1]) ++cur;
+  int o = t - tb.lv_start[cur];
+  int b, tl;
+  if (o < tb.nt_lo[cur]) {
+    b = tb.lo_b[cur];
+    tl = o;
+  } else {
+    b = tb.hi_b[cur];
+    tl = o - tb.nt_lo[cur];
+  }
+  Item it;
+  it.tile = static_cast<int64_t>(tb.tile_off[b]) + tl;
+  it.level = cur;
+  int rem = tb.bcount[b] - tl * kTile;
+  it.nvalid = rem < kTile ? rem : kTile;
+  return it;
+}
+
+template <int WARPS, int CAP>
+struct Smem {
+  static constexpr size_t ring = static_cast<size_t>(WARPS) * kStages * kTileBytes;
+  static constexpr size_t bufs = static_cast<size_t>(WARPS) * CAP * 8;
+  static constexpr size_t bars = static_cast<size_t>(WARPS) * kStages * 8;
+  static constexpr size_t total = ring + bufs + bars + sizeof(Tables);
+  static_assert(ring + bufs >= (kFinCap + kTieCap) * 8, "merge scratch must fit in the scan buffers");
+};
+
+// ---------------------------------------------------------------------- kernel
+template <int WARPS, int CAP>
+__global__ void __launch_bounds__(WARPS * 32, 1)
+    scan_single_kernel(DevLib lib, const uint64_t* __restrict__ query, int k, ScanState* st,
+                       unsigned long long* __restrict__ cand, int32_t* __restrict__ out_idx,
+                       int32_t* __restrict__ out_dist, int32_t* __restrict__ out_count, uint32_t* err,
+                       uint64_t timeout_ns) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  using L = Smem<WARPS, CAP>;
+  unsigned char* ring_all = smem;
+  unsigned long long* bufs_all = reinterpret_cast<unsigned long long*>(smem + L::ring);
+  uint64_t* bars_all = reinterpret_cast<uint64_t*>(smem + L::ring + L::bufs);
+  Tables& tb = *reinterpret_cast<Tables*>(smem + L::ring + L::bufs + L::bars);
+
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5;
+  const int lane = tid & 31;
+  const uint64_t q0 = __ldg(query + 0), q1 = __ldg(query + 1), q2 = __ldg(query + 2);
+  const int pq = __popcll(q0) + __popcll(q1) + __popcll(q2);
+  const uint64_t deadline = global_ns() + timeout_ns;
+
+  // ---- visit-order tables (nearest popcount buckets first)
+  if (lib.bucketed) {
+    for (int b = tid; b < kNumBuckets; b += blockDim.x) {
+      tb.tile_off[b] = lib.tile_off[b];
+      tb.bcount[b] = lib.bcount[b];
+    }
+  }
+  __syncthreads();
+  if (warp == 0) {
+    if (lib.bucketed) {
+      const int nlev = 1 + (pq > kBits - pq ? pq : kBits - pq);
+      uint32_t carry = 0;
+      for (int c = 0; c < 6; ++c) {
+        int lv = c * 32 + lane;
+        int lo = -1, hi = -1, ntl = 0, nth = 0;
+        if (lv < nlev) {
+          lo = pq - lv >= 0 ? pq - lv : -1;
+          hi = (lv > 0 && pq + lv <= kBits) ? pq + lv : -1;
+          ntl = lo >= 0 ? tiles_of(tb.bcount[lo]) : 0;
+          nth = hi >= 0 ? tiles_of(tb.bcount[hi]) : 0;
+        }
+        uint32_t v = static_cast<uint32_t>(ntl + nth);
+        for (int o = 1; o < 32; o <<= 1) {
+          uint32_t t = __shfl_up_sync(kFull, v, o);
+          if (lane >= o) v += t;
+        }
+        v += carry;
+        if (lv < nlev) {
+          tb.lo_b[lv] = lo;
+          tb.hi_b[lv] = hi;
+          tb.nt_lo[lv] = ntl;
+          tb.lv_start[lv + 1] = static_cast<int>(v);
+        }
+        carry = __shfl_sync(kFull, v, 31);
+      }
+      __syncwarp();
+      if (lane == 0) {
+        tb.lv_start[0] = 0;
+        tb.nlev = nlev;
+        tb.lv_start[nlev + 1] = tb.lv_start[nlev];  // sentinel level: never entered
+      }
+    } else if (lane == 0) {
+      tb.tile_off[0] = 0;
+      tb.bcount[0] = static_cast<int>(lib.n);
+      tb.lo_b[0] = 0;
+      tb.hi_b[0] = -1;
+      tb.nt_lo[0] = tiles_of(static_cast<int>(lib.n));
+      tb.lv_start[0] = 0;
+      tb.lv_start[1] = tb.nt_lo[0];
+      tb.lv_start[2] = tb.nt_lo[0];
+      tb.nlev = 1;
+    }
+    if (lane == 0) {
+      tb.is_last = 0;
+      tb.nfin = 0;
+      tb.ntie = 0;
+    }
+  }
+  if (lane == 0) {
+    for (int s = 0; s < kStages; ++s) mbar_init(&bars_all[warp * kStages + s], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  // ---- per-warp streaming scan
+  unsigned char* ring = ring_all + static_cast<size_t>(warp) * kStages * kTileBytes;
+  uint64_t* bars = bars_all + warp * kStages;
+  unsigned long long* buf = bufs_all + static_cast<size_t>(warp) * CAP;
+  const int total = tb.lv_start[tb.nlev];
+  const int W = gridDim.x * WARPS;
+  const int gw = blockIdx.x * WARPS + warp;
+  const uint64_t pol = l2_evict_first_policy();
+
+  unsigned long long thr_key = ~0ull;
+  {
+    unsigned long long g = ld_relaxed_u64(&st->thr_key);
+    unsigned long long gd = key_bound_of_dist(ld_relaxed_u32(&st->thr_d));
+    thr_key = g < gd ? g : gd;
+  }
+  int cnt = 0;
+  int n_issued = 0;
+  bool stop_issue = false;
+  bool failed = false;
+  int fail_j = 0;
+  int cur_issue = 0, cur_proc = 0;
+
+  auto try_issue = [&](int j) {
+    if (stop_issue) return;
+    int t = gw + j * W;
+    if (t >= total) {
+      stop_issue = true;
+      return;
+    }
+    Item it = locate(tb, t, cur_issue);
+    if (static_cast<uint32_t>(it.level) > static_cast<uint32_t>(thr_key >> 32)) {
+      stop_issue = true;  // this and every later tile of the warp is too far in popcount
+      return;
+    }
+    if (lane == 0) {
+      uint64_t* bar = &bars[j % kStages];
+      mbar_arrive_expect_tx(bar, kTileBytes);
+      bulk_copy_g2s(ring + (j % kStages) * kTileBytes, lib.words + it.tile * (kWords * kTile), kTileBytes, bar, pol);
+    }
+    n_issued = j + 1;
+  };
+
+  for (int j = 0; j < kStages; ++j) try_issue(j);
+
+  for (int j = 0; j < n_issued; ++j) {
+    // prefetch the global thresholds; they are folded in after this tile
+    unsigned long long g_key = 0, g_d = 0;
+    if (lane == 0) {
+      g_key = ld_relaxed_u64(&st->thr_key);
+      g_d = key_bound_of_dist(ld_relaxed_u32(&st->thr_d));
+    }
+    const int stage = j % kStages;
+    // every lane observes the phase (acquire of the bulk copy's writes); the
+    // verdict is made warp-uniform so no lane leaves the loop alone
+    bool landed = mbar_wait_bounded(&bars[stage], static_cast<uint32_t>((j / kStages) & 1), deadline);
+    if (!__all_sync(kFull, landed)) {
+      failed = true;
+      fail_j = j;
+      break;
+    }
+    Item it = locate(tb, gw + j * W, cur_proc);
+    const uint32_t D = static_cast<uint32_t>(thr_key >> 32);
+    if (static_cast<uint32_t>(it.level) <= D) {
+      const uint64_t* s = reinterpret_cast<const uint64_t*>(ring + stage * kTileBytes);
+      uint32_t d[4];
+      bool c[4];
+      bool any = false;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        int r = lane + 32 * m;
+        uint64_t x0 = s[r], x1 = s[kTile + r], x2 = s[2 * kTile + r];
+        d[m] = __popcll(x0 ^ q0) + __popcll(x1 ^ q1) + __popcll(x2 ^ q2);
+        c[m] = (r < it.nvalid) && (d[m] <= D);
+        any |= c[m];
+      }
+      if (__any_sync(kFull, any)) {
+        bool added = false;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          unsigned long long key = ~0ull;
+          bool acc = false;
+          if (c[m]) {
+            int32_t idx = __ldg(lib.perm + it.tile * kTile + lane + 32 * m);
+            key = (static_cast<unsigned long long>(d[m]) << 32) | static_cast<uint32_t>(idx);
+            acc = key <= thr_key;
+          }
+          uint32_t bal = __ballot_sync(kFull, acc);
+          if (acc) {
+            buf[cnt + __popc(bal & lanemask_lt())] = key;
+            red_add_u32(&st->hist[d[m]], 1u);
+          }
+          cnt += __popc(bal);
+          added |= bal != 0;
+        }
+        __syncwarp();
+        if (added) {
+          uint32_t Dstar = bound_from_hist(st, k, lane);
+          if (Dstar < 167u) {
+            unsigned long long nk = key_bound_of_dist(Dstar);
+            if (nk < thr_key) {
+              thr_key = nk;
+              if (lane == 0) atomicMin(&st->thr_d, Dstar);
+            }
+          }
+        }
+        if (cnt > CAP - kTile) cnt = compact_buffer(buf, cnt, k, thr_key, st, lane);
+      }
+    }
+    g_key = __shfl_sync(kFull, g_key, 0);
+    g_d = __shfl_sync(kFull, g_d, 0);
+    if (g_key < thr_key) thr_key = g_key;
+    if (g_d < thr_key) thr_key = g_d;
+    __syncwarp();
+    try_issue(j + kStages);
+  }
+
+  if (failed) {
+    // stop issuing; wait (bounded) for every copy still in flight before leaving
+    if (lane == 0) atomicOr(err, DEVERR_TIMEOUT);
+    // items fail_j .. n_issued-1 are the copies not yet consumed; each is the
+    // next phase of its stage, so waiting on that phase is well defined
+    const uint64_t drain_deadline = global_ns() + timeout_ns;
+    for (int j = fail_j; j < n_issued; ++j)
+      mbar_wait_bounded(&bars[j % kStages], static_cast<uint32_t>((j / kStages) & 1), drain_deadline);
+  }
+
+  // final per-warp selection, then hand the candidates to the merge
+  cnt = compact_buffer(buf, cnt, k, thr_key, st, lane);
+  {
+    uint32_t base = 0;
+    if (lane == 0 && cnt > 0) base = atomicAdd(&st->ncand, static_cast<uint32_t>(cnt));
+    base = __shfl_sync(kFull, base, 0);
+    for (int i = lane; i < cnt; i += 32) cand[base + i] = buf[i];
+  }
+
+  // ---- last block merges
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) {
+    unsigned prev = atomicAdd(&st->done, 1u);
+    tb.is_last = (prev == gridDim.x - 1) ? 1 : 0;
+  }
+  __syncthreads();
+  if (!tb.is_last) return;
+  __threadfence();
+
+  unsigned long long* fin = reinterpret_cast<unsigned long long*>(smem);
+  unsigned long long* ties = fin + kFinCap;
+  const int k_eff = static_cast<int>(k < lib.n ? k : lib.n);
+  int* hs = tb.lo_b;  // reuse: 167 ints
+  for (int b = tid; b < kNumBuckets; b += blockDim.x) hs[b] = static_cast<int>(ld_relaxed_u32(&st->hist[b]));
+  __syncthreads();
+  if (tid == 0) {
+    long long run = 0;
+    int T = kNumBuckets;
+    for (int b = 0; b < kNumBuckets; ++b) {
+      if (run + hs[b] >= k_eff) {
+        T = b;
+        break;
+      }
+      run += hs[b];
+    }
+    tb.T = T;
+    tb.cless = static_cast<int>(run);
+  }
+  __syncthreads();
+  const uint32_t T = static_cast<uint32_t>(tb.T);
+  const int cless = tb.cless;
+  const int need = k_eff - cless;  // smallest indices still needed at distance T
+  const uint32_t ncand = ld_relaxed_u32(&st->ncand);
+  for (uint32_t i = tid; i < ncand; i += blockDim.x) {
+    unsigned long long key = __ldcg(cand + i);
+    uint32_t dd = static_cast<uint32_t>(key >> 32);
+    if (dd < T) {
+      int p = atomicAdd(&tb.nfin, 1);
+      if (p < kFinCap) fin[p] = key;
+    } else if (dd == T) {
+      int p = atomicAdd(&tb.ntie, 1);
+      if (p < kTieCap) ties[p] = key;
+    }
+  }
+  __syncthreads();
+  if (tid == 0 && (tb.nfin != cless || tb.T >= kNumBuckets || tb.ntie < need)) atomicOr(err, DEVERR_INTERNAL);
+  const int ntie = tb.ntie;
+  if (need > 0) {
+    if (ntie <= kTieCap) {
+      int p = next_pow2(ntie);
+      for (int i = ntie + tid; i < p; i += blockDim.x) ties[i] = ~0ull;
+      __syncthreads();
+      block_bitonic_sort(ties, p);
+      for (int i = tid; i < need; i += blockDim.x)
+        if (cless + i < kFinCap) fin[cless + i] = ties[i];
+    } else {
+      // Many equal distances: find the need-th smallest index at distance T by bisection.
+      __shared__ int s_cnt;
+      uint32_t lo = 0, hi = 0x7FFFFFFFu;
+      while (lo < hi) {
+        uint32_t mid = lo + (hi - lo) / 2;
+        if (tid == 0) s_cnt = 0;
+        __syncthreads();
+        int local = 0;
+        for (uint32_t i = tid; i < ncand; i += blockDim.x) {
+          unsigned long long key = __ldcg(cand + i);
+          local += (static_cast<uint32_t>(key >> 32) == T) && (static_cast<uint32_t>(key) <= mid);
+        }
+        atomicAdd(&s_cnt, local);
+        __syncthreads();
+        if (s_cnt >= need)
+          hi = mid;
+        else
+          lo = mid + 1;
+        __syncthreads();
+      }
+      if (tid == 0) tb.nfin = cless;
+      __syncthreads();
+      for (uint32_t i = tid; i < ncand; i += blockDim.x) {
+        unsigned long long key = __ldcg(cand + i);
+        if (static_cast<uint32_t>(key >> 32) == T && static_cast<uint32_t>(key) <= lo) {
+          int p = atomicAdd(&tb.nfin, 1);
+          if (p < kFinCap) fin[p] = key;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  {
+    int p = next_pow2(k_eff);
+    for (int i = k_eff + tid; i < p; i += blockDim.x) fin[i] = ~0ull;
+    __syncthreads();
+    block_bitonic_sort(fin, p);
+    for (int i = tid; i < k_eff; i += blockDim.x) {
+      out_idx[i] = static_cast<int32_t>(fin[i] & 0xFFFFFFFFull);
+      out_dist[i] = static_cast<int32_t>(fin[i] >> 32);
+    }
+    if (tid == 0) *out_count = k_eff;
+  }
+  // restore the scan state for the next search on this workspace
+  for (int b = tid; b < 168; b += blockDim.x) st->hist[b] = 0u;
+  if (tid == 0) {
+    st->thr_key = ~0ull;
+    st->thr_d = 166u;
+    st->ncand = 0u;
+    st->done = 0u;
+  }
+}
+
+__global__ void scan_state_init_kernel(ScanState* st) {
+  for (int b = threadIdx.x; b < 168; b += blockDim.x) st->hist[b] = 0u;
+  if (threadIdx.x == 0) {
+    st->thr_key = ~0ull;
+    st->thr_d = 166u;
+    st->done = 0u;
+    st->ncand = 0u;
+  }
+}
+
+template <int WARPS, int CAP>
+cudaError_t launch_cfg(const DevLib& lib, const uint64_t* q, int k, ScanState* st, unsigned long long* cand,
+                       int32_t* oi, int32_t* od, int32_t* oc, uint32_t* err, int num_sms, uint64_t tns,
+                       cudaStream_t s) {
+  using L = Smem<WARPS, CAP>;
+  auto kern = scan_single_kernel<WARPS, CAP>;
+  static bool configured = false;  // attribute set once per process (idempotent)
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(L::total));
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  kern<<<num_sms, WARPS * 32, L::total, s>>>(lib, q, k, st, cand, oi, od, oc, err, tns);
+  return cudaGetLastError();
+}
+
+constexpr int kSmallWarps = 16, kSmallCap = 256;   // k <= 128
+constexpr int kLargeWarps = 8, kLargeCap = 2048;   // k <= 1920
+
+}  // namespace
+
+ScanConfig scan_config_for(int k) {
+  if (k <= kSmallCap - kTile)
+    return {kSmallWarps, kSmallCap, kSmallCap - kTile, Smem<kSmallWarps, kSmallCap>::total};
+  return {kLargeWarps, kLargeCap, kLargeCap - kTile, Smem<kLargeWarps, kLargeCap>::total};
+}
+
+size_t scan_cand_capacity(int num_sms) {
+  size_t a = static_cast<size_t>(num_sms) * kSmallWarps * (kSmallCap - kTile);
+  size_t b = static_cast<size_t>(num_sms) * kLargeWarps * (kLargeCap - kTile);
+  return a > b ? a : b;
+}
+
+cudaError_t scan_state_init(ScanState* st, cudaStream_t s) {
+  scan_state_init_kernel<<<1, 192, 0, s>>>(st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scan_single(const DevLib& lib, const uint64_t* d_query, int k, ScanState* st,
+                               unsigned long long* cand, int32_t* out_idx, int32_t* out_dist, int32_t* out_count,
+                               uint32_t* err, int num_sms, double timeout_s, cudaStream_t s) {
+  uint64_t tns = static_cast<uint64_t>((timeout_s > 0 ? timeout_s : 2.0) * 1e9);
+  if (k <= kSmallCap - kTile)
+    return launch_cfg<kSmallWarps, kSmallCap>(lib, d_query, k, st, cand, out_idx, out_dist, out_count, err, num_sms,
+                                              tns, s);
+  return launch_cfg<kLargeWarps, kLargeCap>(lib, d_query, k, st, cand, out_idx, out_dist, out_count, err, num_sms,
+                                            tns, s);
+}
+
+}  // namespace fps

@@ -44,7 +44,7 @@ PROFILE = os.path.join(ROOT, "profiles", "scan_single_popc_95M.md")
 def parse_args():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--steps", type=int, default=200)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--n", type=int, default=PAPER_N, help="library records")
@@ -280,11 +280,11 @@ def run_gb300(args):
         # algorithmic bytes of the bucketed scan: every record whose popcount bucket is
         # within the final k-th distance of the query, 24 B each, plus k result keys
         bc = info["bucket_count"]
-        pq = np.unpackbits(qs.view(np.uint8), axis=1, bitorder="little")[:, :166].sum(1)
-        tk = dd[:, -1]
+        pq = np.unpackbits(qs.view(np.uint8), axis=1, bitorder="little")[:, :166].sum(1).astype(np.int64)
+        tk = dd[:, -1].astype(np.int64)
         alg = []
         for j in range(QUERIES_PER_STEP):
-            lo, hi = max(0, pq[j] - tk[j]), min(166, pq[j] + tk[j])
+            lo, hi = int(max(0, pq[j] - tk[j])), int(min(166, pq[j] + tk[j]))
             alg.append(24.0 * bc[lo:hi + 1].sum() + 8.0 * K)
         alg_bytes = float(np.mean(alg))
         avg_launch_s = float(np.mean(launch_ms)) / 1e3
@@ -313,7 +313,7 @@ def run_gb300(args):
                         "d2h_bytes_per_step": QUERIES_PER_STEP * (8 + 8 * K)},
                 "gpu_launches": args.steps * QUERIES_PER_STEP}
         if not args.no_cpu_baseline and ws == 1:
-            line["cpu_baseline"] = cpu_oracle_throughput(2_000_000, 4, "")
+            line["cpu_baseline"] = cpu_oracle_throughput(4_000_000, 8, "")
         print(json.dumps(line), flush=True)
     fps.fps_release(lib)
     if ws > 1:

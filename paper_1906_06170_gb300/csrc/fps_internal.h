@@ -41,16 +41,21 @@ struct DevLib {
 };
 
 // Running state of one single-query scan.  Lives at the start of a per-stream
-// workspace; the last block of every scan restores it to the initial values, so
-// consecutive scans on one stream need no memset.
+// workspace (256-byte aligned); the last block of every scan restores it to
+// the initial values, so consecutive scans on one stream need no memset.
+// The first 16 bytes (the two thresholds) are fetched by the bulk copy of every
+// scan tile, so warps see tightened thresholds without a dependent load.
 struct ScanState {
-  uint32_t hist[168];            // accepted records per distance (distinct records)
   unsigned long long thr_key;    // upper bound on the k-th key (d << 32 | index)
   uint32_t thr_d;                // upper bound on the k-th distance
+  uint32_t pad0;
   uint32_t done;                 // blocks finished
   uint32_t ncand;                // keys written to the candidate array
-  uint32_t pad[5];
+  uint32_t pad1[2];
+  uint32_t hist[168];            // accepted records per distance (distinct records)
+  uint32_t queue[16 * 32];       // tail work queues: counter c at queue[32 c] (one 128-byte line each)
 };
+static_assert(sizeof(ScanState) % 16 == 0, "ScanState keeps 16-byte alignment");
 
 // Per-stream staging for host-IO searches; device copy and pinned host copy
 // share the layout so one copy moves each direction.

@@ -37,6 +37,20 @@ namespace {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr int kStages = 3;
+// one ring stage: a 3 KB tile followed by the 16-byte threshold block of the
+// scan state, both delivered by bulk copies that complete on the stage's mbarrier
+constexpr int kThrBytes = 16;
+// Work distribution.  Items (3 KB tiles in visit order) are swept front to
+// back by the whole grid, so at any moment all warps read one contiguous
+// window of the library.  The first kStaticNum/kStaticDen of the items are
+// dealt round-robin (warp w takes w, w + W, w + 2W, ...); the rest are handed
+// out one by one, still in sweep order, by kQueues counters on separate cache
+// lines (warp w draws from counter w % kQueues), so warps the memory system
+// serves faster take more of the tail.  Each warp keeps two requests in flight
+// so the atomics' latency stays hidden.
+constexpr int kStaticNum = 3, kStaticDen = 4;
+constexpr int kQueues = 16;
+constexpr int kStageBytes = kTileBytes + kThrBytes;
 constexpr int kTieCap = 16384;          // tie keys sorted in shared memory by the merge
 constexpr int kFinCap = 2048;           // >= FPS_K_MAX, power of two
 
@@ -85,6 +99,12 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 __device__ __forceinline__ uint64_t l2_evict_first_policy() {
   uint64_t pol;
   asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+
+__device__ __forceinline__ uint64_t l2_evict_last_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
   return pol;
 }
 
@@ -201,25 +221,61 @@ __device__ int compact_buffer(unsigned long long* buf, int cnt, int k, unsigned 
 }
 
 // The smallest D with at least k accepted records at distance <= D; 167 if none.
+// Lane l reads bins 6l .. 6l+5 in one round trip (L2, bypassing L1).
 __device__ uint32_t bound_from_hist(const ScanState* st, int k, int lane) {
-  uint32_t carry = 0;
-  uint32_t found = 167;
-  for (int c = 0; c < 6; ++c) {
-    int b = c * 32 + lane;
-    uint32_t v = b < kNumBuckets ? ld_relaxed_u32(&st->hist[b]) : 0u;
-    for (int o = 1; o < 32; o <<= 1) {
-      uint32_t t = __shfl_up_sync(kFull, v, o);
-      if (lane >= o) v += t;
+  uint32_t h[6] = {0, 0, 0, 0, 0, 0};
+  if (lane < 28) {
+    const uint2* p = reinterpret_cast<const uint2*>(st->hist + 6 * lane);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      uint2 v = __ldcg(p + i);
+      h[2 * i] = v.x;
+      h[2 * i + 1] = v.y;
     }
-    v += carry;
-    uint32_t bal = __ballot_sync(kFull, v >= static_cast<uint32_t>(k));
-    if (bal && found == 167) found = c * 32 + __ffs(bal) - 1;
-    carry = __shfl_sync(kFull, v, 31);
   }
-  return found;
+  uint32_t sum = h[0] + h[1] + h[2] + h[3] + h[4] + h[5];
+  uint32_t incl = sum;
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t t = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += t;
+  }
+  uint32_t bal = __ballot_sync(kFull, incl >= static_cast<uint32_t>(k));
+  if (!bal) return 167u;
+  const int src = __ffs(bal) - 1;
+  uint32_t found = 167u;
+  if (lane == src) {
+    uint32_t run = incl - sum;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      run += h[i];
+      if (run >= static_cast<uint32_t>(k) && found == 167u) found = 6 * lane + i;
+    }
+  }
+  return __shfl_sync(kFull, found, src);
+}
+
+// Move the block's pending histogram counts to the global histogram.  The
+// exchange makes each count leave shared memory exactly once, whichever warps
+// flush concurrently.
+__device__ __forceinline__ void flush_hist(uint32_t* sh_hist, ScanState* st, int lane) {
+  for (int b = lane; b < kNumBuckets; b += 32) {
+    uint32_t v = atomicExch(&sh_hist[b], 0u);
+    if (v) red_add_u32(&st->hist[b], v);
+  }
+  __syncwarp();
+}
+
+// Count accepted records of one warp step in the block's shared histogram,
+// one shared atomic per distinct distance.
+__device__ __forceinline__ void count_accepted(uint32_t* sh_hist, bool acc, uint32_t bal, uint32_t d) {
+  if (acc) {
+    uint32_t same = __match_any_sync(bal, d);
+    if ((same & lanemask_lt()) == 0) atomicAdd(&sh_hist[d], static_cast<uint32_t>(__popc(same)));
+  }
 }
 
 struct Tables {
+  uint32_t sh_hist[168];          // accepted records per distance, not yet added to the global histogram
   int lv_start[kNumBuckets + 2];  // items before level L (level = |popc q - bucket|)
   int lo_b[kNumBuckets + 1];      // bucket popc q - L, or -1
   int hi_b[kNumBuckets + 1];      // bucket popc q + L, or -1
@@ -263,10 +319,11 @@ __device__ __forceinline__ Item locate(const Tables& tb, int t, int& cur) {
 
 template <int WARPS, int CAP>
 struct Smem {
-  static constexpr size_t ring = static_cast<size_t>(WARPS) * kStages * kTileBytes;
+  static constexpr size_t ring = static_cast<size_t>(WARPS) * kStages * kStageBytes;
   static constexpr size_t bufs = static_cast<size_t>(WARPS) * CAP * 8;
   static constexpr size_t bars = static_cast<size_t>(WARPS) * kStages * 8;
-  static constexpr size_t total = ring + bufs + bars + sizeof(Tables);
+  static constexpr size_t items = static_cast<size_t>(WARPS) * kStages * 4;
+  static constexpr size_t total = ring + bufs + bars + items + sizeof(Tables);
   static_assert(ring + bufs >= (kFinCap + kTieCap) * 8, "merge scratch must fit in the scan buffers");
 };
 
@@ -282,7 +339,8 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
   unsigned char* ring_all = smem;
   unsigned long long* bufs_all = reinterpret_cast<unsigned long long*>(smem + L::ring);
   uint64_t* bars_all = reinterpret_cast<uint64_t*>(smem + L::ring + L::bufs);
-  Tables& tb = *reinterpret_cast<Tables*>(smem + L::ring + L::bufs + L::bars);
+  int* items_all = reinterpret_cast<int*>(smem + L::ring + L::bufs + L::bars);
+  Tables& tb = *reinterpret_cast<Tables*>(smem + L::ring + L::bufs + L::bars + L::items);
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
@@ -292,6 +350,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
   const uint64_t deadline = global_ns() + timeout_ns;
 
   // ---- visit-order tables (nearest popcount buckets first)
+  for (int b = tid; b < 168; b += blockDim.x) tb.sh_hist[b] = 0u;
   if (lib.bucketed) {
     for (int b = tid; b < kNumBuckets; b += blockDim.x) {
       tb.tile_off[b] = lib.tile_off[b];
@@ -356,13 +415,18 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
   __syncthreads();
 
   // ---- per-warp streaming scan
-  unsigned char* ring = ring_all + static_cast<size_t>(warp) * kStages * kTileBytes;
+  unsigned char* ring = ring_all + static_cast<size_t>(warp) * kStages * kStageBytes;
   uint64_t* bars = bars_all + warp * kStages;
+  int* stage_item = items_all + warp * kStages;
   unsigned long long* buf = bufs_all + static_cast<size_t>(warp) * CAP;
   const int total = tb.lv_start[tb.nlev];
   const int W = gridDim.x * WARPS;
   const int gw = blockIdx.x * WARPS + warp;
+  const int per_warp_static = static_cast<int>(static_cast<long long>(total) * kStaticNum / kStaticDen / W);
+  const int dyn_base = per_warp_static * W;          // first item of the queued tail
+  uint32_t* my_queue = &st->queue[32 * (gw % kQueues)];
   const uint64_t pol = l2_evict_first_policy();
+  const uint64_t pol_keep = l2_evict_last_policy();
 
   unsigned long long thr_key = ~0ull;
   {
@@ -377,22 +441,44 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
   int fail_j = 0;
   int cur_issue = 0, cur_proc = 0;
 
+  // issue side: j-th item of the warp; tail items come from the warp's queue,
+  // requested two items ahead (lane 0 holds the pending queue positions)
+  int issue_j = 0;
+  uint32_t pend0 = 0, pend1 = 0;
+  if (lane == 0 && dyn_base < total) {
+    pend0 = atomicAdd(my_queue, 1u);
+    pend1 = atomicAdd(my_queue, 1u);
+  }
   auto try_issue = [&](int j) {
     if (stop_issue) return;
-    int t = gw + j * W;
+    int t;
+    if (issue_j < per_warp_static) {
+      t = gw + issue_j * W;
+    } else {
+      uint32_t r = __shfl_sync(kFull, pend0, 0);
+      t = dyn_base + (gw % kQueues) + kQueues * static_cast<int>(r);
+      if (t < total && lane == 0) {
+        pend0 = pend1;
+        pend1 = atomicAdd(my_queue, 1u);
+      }
+    }
     if (t >= total) {
       stop_issue = true;
       return;
     }
     Item it = locate(tb, t, cur_issue);
     if (static_cast<uint32_t>(it.level) > static_cast<uint32_t>(thr_key >> 32)) {
-      stop_issue = true;  // this and every later tile of the warp is too far in popcount
+      stop_issue = true;  // this and every later item is too far in popcount
       return;
     }
+    ++issue_j;
     if (lane == 0) {
       uint64_t* bar = &bars[j % kStages];
-      mbar_arrive_expect_tx(bar, kTileBytes);
-      bulk_copy_g2s(ring + (j % kStages) * kTileBytes, lib.words + it.tile * (kWords * kTile), kTileBytes, bar, pol);
+      unsigned char* dst = ring + (j % kStages) * kStageBytes;
+      stage_item[j % kStages] = t;
+      mbar_arrive_expect_tx(bar, kStageBytes);
+      bulk_copy_g2s(dst, lib.words + it.tile * (kWords * kTile), kTileBytes, bar, pol);
+      bulk_copy_g2s(dst + kTileBytes, &st->thr_key, kThrBytes, bar, pol_keep);
     }
     n_issued = j + 1;
   };
@@ -400,12 +486,6 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
   for (int j = 0; j < kStages; ++j) try_issue(j);
 
   for (int j = 0; j < n_issued; ++j) {
-    // prefetch the global thresholds; they are folded in after this tile
-    unsigned long long g_key = 0, g_d = 0;
-    if (lane == 0) {
-      g_key = ld_relaxed_u64(&st->thr_key);
-      g_d = key_bound_of_dist(ld_relaxed_u32(&st->thr_d));
-    }
     const int stage = j % kStages;
     // every lane observes the phase (acquire of the bulk copy's writes); the
     // verdict is made warp-uniform so no lane leaves the loop alone
@@ -415,10 +495,19 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
       fail_j = j;
       break;
     }
-    Item it = locate(tb, gw + j * W, cur_proc);
+    const unsigned char* sb = ring + stage * kStageBytes;
+    {
+      // thresholds as they were when this tile was issued (never looser than the truth)
+      unsigned long long g_key = *reinterpret_cast<const unsigned long long*>(sb + kTileBytes);
+      uint32_t g_d = *reinterpret_cast<const uint32_t*>(sb + kTileBytes + 8);
+      unsigned long long gd = key_bound_of_dist(g_d);
+      if (g_key < thr_key) thr_key = g_key;
+      if (gd < thr_key) thr_key = gd;
+    }
+    Item it = locate(tb, stage_item[stage], cur_proc);
     const uint32_t D = static_cast<uint32_t>(thr_key >> 32);
     if (static_cast<uint32_t>(it.level) <= D) {
-      const uint64_t* s = reinterpret_cast<const uint64_t*>(ring + stage * kTileBytes);
+      const uint64_t* s = reinterpret_cast<const uint64_t*>(sb);
       uint32_t d[4];
       bool c[4];
       bool any = false;
@@ -430,7 +519,42 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
         c[m] = (r < it.nvalid) && (d[m] <= D);
         any |= c[m];
       }
-      if (__any_sync(kFull, any)) {
+      if (j == 0 && k < kTile) {
+        // First tile of the warp: keep only its own k best records.  A tile lies
+        // inside one popcount bucket, where position order is index order, so
+        // sorting (d, position) orders exactly like (d, index).  Dropped records
+        // are worse than k records of this tile, hence never in the top k.
+        if (__any_sync(kFull, any)) {
+#pragma unroll
+          for (int m = 0; m < 4; ++m)
+            buf[lane + 32 * m] = c[m] ? ((static_cast<unsigned long long>(d[m]) << 32) | (lane + 32 * m)) : ~0ull;
+          __syncwarp();
+          warp_bitonic_sort(buf, kTile, lane);
+          int kept = 0;
+          for (int base = 0; base < k; base += 32) {
+            int i = base + lane;
+            unsigned long long e = i < k ? buf[i] : ~0ull;
+            bool acc = e != ~0ull;
+            uint32_t dd = static_cast<uint32_t>(e >> 32);
+            uint32_t bal = __ballot_sync(kFull, acc);
+            if (acc) {
+              int32_t idx = __ldg(lib.perm + it.tile * kTile + static_cast<int>(e & 0xFFull));
+              buf[i] = (static_cast<unsigned long long>(dd) << 32) | static_cast<uint32_t>(idx);
+            }
+            count_accepted(tb.sh_hist, acc, bal, dd);
+            kept += __popc(bal);
+          }
+          __syncwarp();
+          cnt = kept;
+          if (kept == k && buf[k - 1] < thr_key) thr_key = buf[k - 1];
+          flush_hist(tb.sh_hist, st, lane);
+          uint32_t Dstar = bound_from_hist(st, k, lane);
+          if (Dstar < 167u && key_bound_of_dist(Dstar) < thr_key) {
+            thr_key = key_bound_of_dist(Dstar);
+            if (lane == 0) atomicMin(&st->thr_d, Dstar);
+          }
+        }
+      } else if (__any_sync(kFull, any)) {
         bool added = false;
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
@@ -442,15 +566,14 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
             acc = key <= thr_key;
           }
           uint32_t bal = __ballot_sync(kFull, acc);
-          if (acc) {
-            buf[cnt + __popc(bal & lanemask_lt())] = key;
-            red_add_u32(&st->hist[d[m]], 1u);
-          }
+          if (acc) buf[cnt + __popc(bal & lanemask_lt())] = key;
+          count_accepted(tb.sh_hist, acc, bal, d[m]);
           cnt += __popc(bal);
           added |= bal != 0;
         }
         __syncwarp();
         if (added) {
+          flush_hist(tb.sh_hist, st, lane);
           uint32_t Dstar = bound_from_hist(st, k, lane);
           if (Dstar < 167u) {
             unsigned long long nk = key_bound_of_dist(Dstar);
@@ -463,10 +586,6 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
         if (cnt > CAP - kTile) cnt = compact_buffer(buf, cnt, k, thr_key, st, lane);
       }
     }
-    g_key = __shfl_sync(kFull, g_key, 0);
-    g_d = __shfl_sync(kFull, g_d, 0);
-    if (g_key < thr_key) thr_key = g_key;
-    if (g_d < thr_key) thr_key = g_d;
     __syncwarp();
     try_issue(j + kStages);
   }
@@ -490,7 +609,9 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
     for (int i = lane; i < cnt; i += 32) cand[base + i] = buf[i];
   }
 
-  // ---- last block merges
+  // ---- pending counts to the global histogram, then the last block merges
+  __syncthreads();
+  if (warp == 0) flush_hist(tb.sh_hist, st, lane);
   __threadfence();
   __syncthreads();
   if (tid == 0) {
@@ -599,6 +720,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
     st->ncand = 0u;
     st->done = 0u;
   }
+  for (int c = tid; c < kQueues; c += blockDim.x) st->queue[32 * c] = 0u;
 }
 
 __global__ void scan_state_init_kernel(ScanState* st) {
@@ -609,6 +731,7 @@ __global__ void scan_state_init_kernel(ScanState* st) {
     st->done = 0u;
     st->ncand = 0u;
   }
+  for (int c = threadIdx.x; c < kQueues; c += blockDim.x) st->queue[32 * c] = 0u;
 }
 
 template <int WARPS, int CAP>

@@ -180,6 +180,31 @@ fps_status fps_search_batch(fps_library lib, const uint64_t* queries, int Q, con
                             const int64_t* out_offsets, int32_t* out_index, int32_t* out_dist, int32_t* out_count,
                             const fps_search_opts* opts, void* cuda_stream);
 
+/*
+ * Single-query search that allocates no device memory (the paper has no
+ * counterpart: it exists for callers that cannot allocate when they search --
+ * code whose device memory is all owned by another allocator, code with a
+ * hard latency budget that cannot take a cudaMalloc and its implicit
+ * synchronisation, code that searches on many short-lived streams where
+ * fps_search_packed would create a workspace per stream).
+ *
+ * query (FPS_WORDS words), out_index and out_dist (k entries each) and
+ * out_count (one int32) are device pointers owned by the caller; the call
+ * enqueues work on cuda_stream and returns.  Results equal fps_search_packed's.
+ * The scan's scratch is one fixed array inside this library, about 2.6 MB,
+ * that every GPU which loads the library holds until the process exits.
+ * Limits: k <= FPS_NOALLOC_K_MAX and at most 160 SMs (FPS_ERR_UNSUPPORTED
+ * otherwise).  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) -- make that first call before any stream capture.
+ * All calls on a device share the array: calls that may overlap on the GPU
+ * (different streams without ordering between them) race and give wrong
+ * results; order them on one stream.  Each call clears the scratch it needs.
+ * A device-side failure (a bounded wait that ran out) leaves *out_count = -1.
+ */
+#define FPS_NOALLOC_K_MAX 128
+fps_status fps_search_noalloc(fps_library lib, const uint64_t* query, int k, int32_t* out_index, int32_t* out_dist,
+                              int32_t* out_count, void* cuda_stream);
+
 /* Wait for cuda_stream and report (then clear) any device-side error of searches enqueued on it. */
 fps_status fps_sync(fps_library lib, void* cuda_stream);
 

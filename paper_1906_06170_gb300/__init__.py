@@ -16,7 +16,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(_HERE, "libfps.so")
 
-FPS_BITS, FPS_WORDS, FPS_K_MAX = 166, 3, 1920
+FPS_BITS, FPS_WORDS, FPS_K_MAX, FPS_NOALLOC_K_MAX = 166, 3, 1920, 128
 (FPS_OK, FPS_ERR_INVALID_ARG, FPS_ERR_IO, FPS_ERR_PARSE, FPS_ERR_BUDGET, FPS_ERR_CUDA, FPS_ERR_TIMEOUT,
  FPS_ERR_OVERFLOW_INTERNAL, FPS_ERR_UNSUPPORTED, FPS_ERR_NOMEM) = range(10)
 FPS_LOAD_ACCEPT_167, FPS_LOAD_NO_BUCKETS, FPS_LOAD_TC_OPERAND = 0x1, 0x2, 0x4
@@ -71,11 +71,12 @@ _lib.fps_search.argtypes = [_vp, ctypes.c_char_p, _i32, _vp, _vp, _vp, ctypes.PO
 _lib.fps_search_packed.argtypes = [_vp, _vp, _i32, _vp, _vp, _vp, ctypes.POINTER(fps_search_opts), _vp]
 _lib.fps_search_batch.argtypes = [_vp, _vp, _i32, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(fps_search_opts), _vp]
 _lib.fps_sync.argtypes = [_vp, _vp]
+_lib.fps_search_noalloc.argtypes = [_vp, _vp, _i32, _vp, _vp, _vp, _vp]
 _lib.fps_pack_query.argtypes = [ctypes.c_char_p, _vp]
 _lib.fps_pack_text.argtypes = [_vp, ctypes.c_size_t, ctypes.c_uint32, _vp, _vp, ctypes.c_size_t,
                                ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]
 for _f in ("fps_library_load", "fps_release", "fps_library_info_get", "fps_library_cid", "fps_search",
-           "fps_search_packed", "fps_search_batch", "fps_sync", "fps_pack_query", "fps_pack_text"):
+           "fps_search_packed", "fps_search_batch", "fps_sync", "fps_pack_query", "fps_pack_text", "fps_search_noalloc"):
     getattr(_lib, _f).restype = _i32
 
 
@@ -284,6 +285,22 @@ def fps_search_batch(lib: Library, queries, k, *, path: int = FPS_PATH_AUTO, out
                                dist.ctypes.data, cnt.ctypes.data, ctypes.byref(o), _stream_ptr(stream))
     _check(st, "fps_search_batch")
     return [(idx[off[i]: off[i] + cnt[i]].copy(), dist[off[i]: off[i] + cnt[i]].copy()) for i in range(Q)]
+
+
+def fps_search_noalloc(lib: Library, query, k: int, out_index, out_dist, out_count, stream=None):
+    """Single packed query into caller-owned CUDA tensors, with no device allocation by the library.
+
+    For callers that cannot allocate device memory while searching (see
+    include/fps.h).  ``query`` (3 x 64-bit), ``out_index``/``out_dist`` (>= k int32)
+    and ``out_count`` (1 int32) are CUDA tensors; asynchronous on ``stream``.
+    Calls on one device share the library's fixed scratch array, so they must not
+    overlap on the GPU.  ``out_count == -1`` after the stream completes means the
+    search failed on the device.
+    """
+    st = _lib.fps_search_noalloc(lib._h, query.data_ptr(), int(k), out_index.data_ptr(), out_dist.data_ptr(),
+                                 out_count.data_ptr(), _stream_ptr(stream))
+    _check(st, "fps_search_noalloc")
+    return out_index, out_dist, out_count
 
 
 def fps_sync(lib: Library, stream=None):

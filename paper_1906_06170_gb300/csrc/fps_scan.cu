@@ -784,3 +784,114 @@ cudaError_t launch_scan_single(const DevLib& lib, const uint64_t* d_query, int k
 }
 
 }  // namespace fps
+
+// ===========================================================================
+// Single-query search that allocates nothing.
+//
+// Some callers cannot allocate device memory when they search: code whose
+// device memory is entirely owned by another allocator (a framework pool that
+// must account for every byte), code with a hard latency budget where a
+// cudaMalloc and its implicit synchronisation are not acceptable, and code
+// that searches on many short-lived streams, each of which would make
+// fps_search_packed allocate a new per-stream workspace.  For them the scan's
+// scratch (scan state, error word, candidate keys) lives in one file-scope
+// device array of fixed size, kNoAllocBytes, which every GPU that loads this
+// library holds until the process exits.
+// ===========================================================================
+namespace fps {
+namespace {
+
+constexpr int kNoAllocMaxSms = 160;                      // largest grid the array can serve
+constexpr int kNoAllocKMax = kSmallCap - kTile;          // 128: the shared-buffer configuration
+constexpr size_t kNoAllocStateBytes = (sizeof(ScanState) + 255) / 256 * 256;
+constexpr size_t kNoAllocErrBytes = 256;
+constexpr size_t kNoAllocCandKeys = static_cast<size_t>(kNoAllocMaxSms) * kSmallWarps * kNoAllocKMax;
+constexpr size_t kNoAllocBytes = kNoAllocStateBytes + kNoAllocErrBytes + kNoAllocCandKeys * 8;  // ~2.6 MB
+constexpr int kNoAllocMaxDevices = 64;
+
+}  // namespace
+}  // namespace fps
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[fps::kNoAllocBytes];
+
+namespace fps {
+namespace {
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+// Device address of the scratch array on the current device, looked up once per
+// device (host code cannot use the symbol itself as a device pointer).
+cudaError_t noalloc_scratch(int device, unsigned char** out) {
+  if (device < 0 || device >= kNoAllocMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[device]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_addr[device] = p;
+  }
+  *out = static_cast<unsigned char*>(g_noalloc_addr[device]);
+  return cudaSuccess;
+}
+
+// Every call starts from a clean scan state and a cleared error word: the
+// array keeps whatever the previous call (possibly a failed one) left there.
+__global__ void noalloc_prepare_kernel(ScanState* st, uint32_t* err) {
+  for (int b = threadIdx.x; b < 168; b += blockDim.x) st->hist[b] = 0u;
+  for (int c = threadIdx.x; c < kQueues; c += blockDim.x) st->queue[32 * c] = 0u;
+  if (threadIdx.x == 0) {
+    st->thr_key = ~0ull;
+    st->thr_d = 166u;
+    st->done = 0u;
+    st->ncand = 0u;
+    *err = 0u;
+  }
+}
+
+// A device-side failure (a bounded wait that ran out) is reported to the caller
+// as *out_count = -1, since the error word itself is not the caller's memory.
+__global__ void noalloc_finish_kernel(const uint32_t* err, int32_t* out_count) {
+  if (threadIdx.x == 0 && *err != 0u) *out_count = -1;
+}
+
+}  // namespace
+}  // namespace fps
+
+extern "C" fps_status fps_search_noalloc(fps_library lib, const uint64_t* query, int k, int32_t* out_index,
+                                         int32_t* out_dist, int32_t* out_count, void* cuda_stream) {
+  using namespace fps;
+  if (!lib || !query || !out_count || k < 0 || (k > 0 && (!out_index || !out_dist))) return FPS_ERR_INVALID_ARG;
+  if (k > kNoAllocKMax) return FPS_ERR_UNSUPPORTED;
+  Library* L = reinterpret_cast<Library*>(lib);
+  if (L->num_sms > kNoAllocMaxSms) return FPS_ERR_UNSUPPORTED;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  int prev = -1;
+  if (cudaGetDevice(&prev) != cudaSuccess || cudaSetDevice(L->device) != cudaSuccess) {
+    cudaGetLastError();
+    return FPS_ERR_CUDA;
+  }
+  fps_status status = FPS_OK;
+  unsigned char* base = nullptr;
+  if (noalloc_scratch(L->device, &base) != cudaSuccess) {
+    status = FPS_ERR_CUDA;
+  } else if (L->n == 0 || k == 0) {
+    if (cudaMemsetAsync(out_count, 0, sizeof(int32_t), s) != cudaSuccess) status = FPS_ERR_CUDA;
+  } else {
+    ScanState* st = reinterpret_cast<ScanState*>(base);
+    uint32_t* err = reinterpret_cast<uint32_t*>(base + kNoAllocStateBytes);
+    auto* cand = reinterpret_cast<unsigned long long*>(base + kNoAllocStateBytes + kNoAllocErrBytes);
+    noalloc_prepare_kernel<<<1, 192, 0, s>>>(st, err);
+    if (cudaGetLastError() != cudaSuccess ||
+        launch_cfg<kSmallWarps, kSmallCap>(L->dev, query, k, st, cand, out_index, out_dist, out_count, err,
+                                           L->num_sms, 2000000000ull, s) != cudaSuccess) {
+      status = FPS_ERR_CUDA;
+    } else {
+      noalloc_finish_kernel<<<1, 32, 0, s>>>(err, out_count);
+      if (cudaGetLastError() != cudaSuccess) status = FPS_ERR_CUDA;
+    }
+  }
+  if (status != FPS_OK) cudaGetLastError();
+  cudaSetDevice(prev);
+  return status;
+}

@@ -500,6 +500,127 @@ fps_status batch_sequential(Library* L, Workspace* w, const uint64_t* dq, int Q,
   return FPS_OK;
 }
 
+// Sub-allocation of one staging block: each section 256-byte aligned.
+struct Carve {
+  size_t at = 0;
+  size_t take(size_t bytes) {
+    size_t p = at;
+    at += (bytes + 255) / 256 * 256;
+    return p;
+  }
+};
+
+// Candidate capacity of a query: 32 k + 8192 keys, never more than the library.
+int64_t batch_cap(int k, int64_t n) {
+  if (k <= 0) return 0;
+  int64_t c = 32 * static_cast<int64_t>(k) + 8192;
+  return c < n ? c : n;
+}
+
+// Many queries per launch with the batched kernels (pilot bound, scan, per-query select).
+fps_status batch_kernels(Library* L, Workspace* w, const uint64_t* queries, int Q, const int32_t* k,
+                         const int64_t* off, int64_t total, int32_t* out_index, int32_t* out_dist,
+                         int32_t* out_count, const fps_search_opts* opts, bool dev_io, cudaStream_t s,
+                         int64_t* n_fallback) {
+  std::vector<int64_t> coff(static_cast<size_t>(Q) + 1, 0);
+  for (int q = 0; q < Q; ++q) coff[q + 1] = coff[q] + batch_cap(k[q], L->n);
+  Carve dv;
+  const size_t d_q = dv.take(dev_io ? 0 : sizeof(uint64_t) * 3 * Q);
+  const size_t d_k = dv.take(sizeof(int32_t) * Q);
+  const size_t d_co = dv.take(sizeof(int64_t) * (Q + 1));
+  const size_t d_oo = dv.take(sizeof(int64_t) * (Q + 1));
+  const size_t plan_end = dv.at;
+  const size_t d_thr = dv.take(sizeof(uint32_t) * Q);
+  const size_t d_cnt = dv.take(sizeof(uint32_t) * Q);
+  const size_t d_hist = dv.take(sizeof(uint32_t) * 168 * Q);
+  const size_t d_work = dv.take(sizeof(uint32_t));
+  const size_t d_oi = dv.take(dev_io ? 0 : sizeof(int32_t) * total);
+  const size_t d_od = dv.take(dev_io ? 0 : sizeof(int32_t) * total);
+  const size_t d_oc = dv.take(sizeof(int32_t) * Q);
+  const size_t d_cand = dv.take(sizeof(unsigned long long) * static_cast<size_t>(coff[Q]));
+  const size_t out_begin = dev_io ? d_oc : d_oi, out_end = d_cand;
+  fps_status st = batch_staging(w, dv.at, plan_end > out_end ? plan_end : out_end);
+  if (st != FPS_OK) return st;
+  char* db = static_cast<char*>(w->batch_block);
+  char* hb = static_cast<char*>(w->batch_host);
+  if (!dev_io) std::memcpy(hb + d_q, queries, sizeof(uint64_t) * 3 * Q);
+  std::memcpy(hb + d_k, k, sizeof(int32_t) * Q);
+  std::memcpy(hb + d_co, coff.data(), sizeof(int64_t) * (Q + 1));
+  std::memcpy(hb + d_oo, off, sizeof(int64_t) * (Q + 1));
+  if (cudaMemcpyAsync(db, hb, plan_end, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+    cudaGetLastError();
+    return FPS_ERR_CUDA;
+  }
+  BatchDev b{};
+  b.Q = Q;
+  b.queries = dev_io ? queries : reinterpret_cast<const uint64_t*>(db + d_q);
+  b.k = reinterpret_cast<const int32_t*>(db + d_k);
+  b.cand_off = reinterpret_cast<const int64_t*>(db + d_co);
+  b.out_off = reinterpret_cast<const int64_t*>(db + d_oo);
+  b.thr = reinterpret_cast<uint32_t*>(db + d_thr);
+  b.cnt = reinterpret_cast<uint32_t*>(db + d_cnt);
+  b.hist = reinterpret_cast<uint32_t*>(db + d_hist);
+  b.cand = reinterpret_cast<unsigned long long*>(db + d_cand);
+  b.out_idx = dev_io ? out_index : reinterpret_cast<int32_t*>(db + d_oi);
+  b.out_dist = dev_io ? out_dist : reinterpret_cast<int32_t*>(db + d_od);
+  b.out_count = reinterpret_cast<int32_t*>(db + d_oc);
+  b.err = &w->io->err;
+  if (batch_prepare(L->dev, b, 1, s) != cudaSuccess ||
+      batch_scan_popc(L->dev, b, L->num_sms, reinterpret_cast<uint32_t*>(db + d_work), s) != cudaSuccess ||
+      batch_select(L->dev, b, s) != cudaSuccess) {
+    cudaGetLastError();
+    return FPS_ERR_CUDA;
+  }
+  // results (host form) or just the counts (device form) come back once; queries whose
+  // candidates overflowed (count -2) are re-run exactly with the single-query scan
+  if (cudaMemcpyAsync(hb + out_begin, db + out_begin, out_end - out_begin, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaGetLastError();
+    return FPS_ERR_CUDA;
+  }
+  st = take_device_error(w, s);
+  if (st != FPS_OK) return st;
+  const int32_t* hc = reinterpret_cast<const int32_t*>(hb + d_oc);
+  const double tmo = opt_timeout(opts);
+  int64_t nf = 0;
+  for (int q = 0; q < Q; ++q) {
+    if (hc[q] != -2) continue;
+    ++nf;
+    if (!dev_io) {
+      int32_t c = 0;
+      st = search_one_host(L, queries + 3 * q, k[q], out_index + off[q], out_dist + off[q], &c, opts, s);
+      if (st != FPS_OK) return st;
+      out_count[q] = c;
+    }
+  }
+  if (dev_io) {
+    if (cudaMemcpyAsync(out_count, db + d_oc, sizeof(int32_t) * Q, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+      cudaGetLastError();
+      return FPS_ERR_CUDA;
+    }
+    // the fallback searches (if any) write their own counts after this copy
+    for (int q = 0; q < Q && nf > 0; ++q) {
+      if (hc[q] != -2) continue;
+      if (launch_scan_single(L->dev, queries + 3 * q, k[q], w->st, w->cand, out_index + off[q], out_dist + off[q],
+                             out_count + q, &w->io->err, L->num_sms, tmo, s) != cudaSuccess) {
+        cudaGetLastError();
+        return FPS_ERR_CUDA;
+      }
+    }
+  } else {
+    const int32_t* hi = reinterpret_cast<const int32_t*>(hb + d_oi);
+    const int32_t* hd = reinterpret_cast<const int32_t*>(hb + d_od);
+    for (int q = 0; q < Q; ++q) {
+      if (hc[q] == -2) continue;
+      out_count[q] = hc[q];
+      std::memcpy(out_index + off[q], hi + off[q], sizeof(int32_t) * hc[q]);
+      std::memcpy(out_dist + off[q], hd + off[q], sizeof(int32_t) * hc[q]);
+    }
+  }
+  *n_fallback = nf;
+  return FPS_OK;
+}
+
 fps_status search_batch_impl(Library* L, const uint64_t* queries, int Q, const int32_t* k, const int64_t* off,
                              int64_t total, int32_t* out_index, int32_t* out_dist, int32_t* out_count,
                              const fps_search_opts* opts, bool dev_io, cudaStream_t s) {
@@ -508,6 +629,22 @@ fps_status search_batch_impl(Library* L, const uint64_t* queries, int Q, const i
   fps_status st = get_workspace(L, s, &w);
   if (st != FPS_OK) return st;
   const double tmo = opt_timeout(opts);
+  const int path = opts ? opts->path : FPS_PATH_AUTO;
+  if (path != FPS_PATH_POPC) {
+    if (path != FPS_PATH_AUTO && path != FPS_PATH_POPC_BATCH) return FPS_ERR_UNSUPPORTED;
+    if (!dev_io)
+      for (int q = 0; q < Q; ++q)
+        if (queries[3 * q + 2] >> (kBits - 128)) return FPS_ERR_INVALID_ARG;
+    int64_t nf = 0;
+    st = batch_kernels(L, w, queries, Q, k, off, total, out_index, out_dist, out_count, opts, dev_io, s, &nf);
+    if (st == FPS_OK && opts && opts->stats) {
+      opts->stats->queries = Q;
+      opts->stats->fallbacks = nf;
+      opts->stats->candidates = 0;
+      opts->stats->path_used = FPS_PATH_POPC_BATCH;
+    }
+    return st;
+  }
   if (dev_io) return batch_sequential(L, w, queries, Q, k, off, out_index, out_dist, out_count, tmo, s);
   for (int q = 0; q < Q; ++q)
     if (queries[3 * q + 2] >> (kBits - 128)) return FPS_ERR_INVALID_ARG;

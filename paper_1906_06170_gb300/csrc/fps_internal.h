@@ -97,6 +97,34 @@ struct Library {
   std::map<cudaStream_t, Workspace*> ws;
 };
 
+// Per-query state of a batched search (device pointers; fps_batch.cu).
+//   thr[q]   upper bound on the k-th distance of query q (starts from the pilot
+//            or from a predicted threshold, only ever tightened);
+//   hist[q]  accepted records of q per distance (168 bins, each record once);
+//   cnt[q]   candidate keys appended for q (may exceed its capacity: overflow);
+//   cand     keys d << 32 | index, query q owns [cand_off[q], cand_off[q+1]).
+struct BatchDev {
+  int Q;
+  const uint64_t* queries;       // Q x 3 words
+  const int32_t* k;              // Q
+  const int64_t* cand_off;       // Q + 1
+  const int64_t* out_off;        // Q + 1
+  uint32_t* thr;
+  uint32_t* hist;
+  uint32_t* cnt;
+  unsigned long long* cand;
+  int32_t* out_idx;
+  int32_t* out_dist;
+  int32_t* out_count;            // -2 = candidate overflow (host falls back), else min(k, N)
+  uint32_t* err;
+};
+
+// ---- batched kernels (fps_batch.cu)
+cudaError_t batch_prepare(const DevLib& lib, const BatchDev& b, int use_pilot, cudaStream_t s);
+cudaError_t batch_scan_popc(const DevLib& lib, const BatchDev& b, int num_sms, uint32_t* work_counter,
+                            cudaStream_t s);
+cudaError_t batch_select(const DevLib& lib, const BatchDev& b, cudaStream_t s);
+
 // ---- kernels (fps_scan.cu)
 // Scan configuration chosen for a given k.
 struct ScanConfig {

@@ -49,6 +49,11 @@ def parse_args():
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--n", type=int, default=PAPER_N, help="library records")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--workload", default="single", choices=["single", "batch"],
+                   help="single: 16 sequential single queries per step (default); "
+                        "batch: --queries queries with mixed k in one batched call per step")
+    p.add_argument("--queries", type=int, default=4096)
+    p.add_argument("--path", default="popc_batch", choices=["popc_batch", "popc", "tc_fp8", "tc_i8", "learned"])
     return p.parse_args()
 
 
@@ -320,10 +325,68 @@ def run_gb300(args):
         dist.destroy_process_group()
 
 
+def run_batch(args):
+    """Batched workload: Q queries with k drawn from {1, 10, 30, 100, 1000} in one call per step."""
+    import torch
+
+    import paper_1906_06170_gb300 as fps
+    import synth
+
+    paths = {"popc_batch": fps.FPS_PATH_POPC_BATCH, "popc": fps.FPS_PATH_POPC, "tc_fp8": fps.FPS_PATH_TC_FP8,
+             "tc_i8": fps.FPS_PATH_TC_I8, "learned": fps.FPS_PATH_LEARNED}
+    torch.cuda.set_device(0)
+    n, Q = args.n, args.queries
+    flags = fps.FPS_LOAD_TC_OPERAND if args.path in ("tc_fp8", "tc_i8") else 0
+    lib = fps.fps_library_load(packed=synth.packed(n, 0), flags=flags)
+    qs = synth.packed(Q, synth.query_seed(2))
+    ks = synth.k_mix(Q, seed=2)
+    qd = torch.from_numpy(qs.view(np.int64).copy()).cuda()
+    off = fps.batch_offsets(ks)
+    oi = torch.empty(int(off[-1]), dtype=torch.int32, device="cuda")
+    od = torch.empty_like(oi)
+    oc = torch.empty(Q, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    stats = fps.fps_search_stats()
+
+    def step():
+        fps.fps_search_batch(lib, qd, ks, path=paths[args.path], out_index=oi, out_dist=od, out_count=oc,
+                             offsets=off, stream=stream, stats=stats)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        step()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = t0.elapsed_time(t1) / args.steps
+    cnt = oc.cpu().numpy()
+    assert np.all(cnt == np.minimum(ks, n)), "batch results malformed"
+    value = Q * n / (ms / 1e3) / 1e9
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "queries_per_s": Q / (ms / 1e3), "dtype": "u64" if args.path.startswith("popc") else args.path,
+            "data": "synthetic", "fallbacks": int(stats.fallbacks),
+            "config": {"workload": f"{n:,} generated records (seed 0), {Q} queries (seed 1002) with k from "
+                                   f"{{1,10,30,100,1000}} per batched call, path {args.path}",
+                       "n_records": n, "queries": Q},
+            "clocks": clk}
+    print(json.dumps(line), flush=True)
+    fps.fps_release(lib)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batch(args)
     else:
         run_gb300(args)
 

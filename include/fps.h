@@ -61,7 +61,9 @@ typedef struct fps_library_s* fps_library;
 
 #define FPS_LOAD_ACCEPT_167 0x1u  /* a 167-character line starting with '0' loses that character */
 #define FPS_LOAD_NO_BUCKETS 0x2u  /* keep library order: no popcount buckets, so no pruning */
-#define FPS_LOAD_TC_OPERAND 0x4u  /* also build the 0/1 FP8 operand the tensor-core batch path needs */
+#define FPS_LOAD_TC_OPERAND 0x4u  /* also build the 0/1 FP8 operand the tensor-core batch path needs
+                                     (192 bytes per record, bucketed layout only) */
+#define FPS_LOAD_TC_INT8 0x8u     /* INT8 operand: always FPS_ERR_UNSUPPORTED (sm_103a has no tcgen05 kind::i8) */
 
 /*
  * Exactly one library source must be given: a file path, an in-memory text
@@ -124,7 +126,7 @@ typedef enum {
   FPS_PATH_POPC = 1,     /* popcount scan: one launch per query (single-query kernel) */
   FPS_PATH_POPC_BATCH = 2, /* popcount scan, many queries per launch */
   FPS_PATH_TC_FP8 = 3,   /* tensor-core contraction on 0/1 FP8 operands */
-  FPS_PATH_TC_I8 = 4,    /* tensor-core contraction on 0/1 INT8 operands */
+  FPS_PATH_TC_I8 = 4,    /* INT8 tensor-core contraction: FPS_ERR_UNSUPPORTED on sm_103a (no kind::i8) */
   FPS_PATH_LEARNED = 5   /* predicted per-query threshold, exact fallback */
 } fps_path;
 
@@ -143,7 +145,7 @@ typedef struct {
   int path;                      /* fps_path */
   uint32_t flags;                /* FPS_SEARCH_* */
   double timeout_s;              /* bound on any device-side wait; <= 0 = 2 s */
-  fps_search_stats* stats;       /* optional out (host-IO calls only) */
+  fps_search_stats* stats;       /* optional out (host memory; filled by fps_search_batch in both forms) */
   const float* tau;              /* FPS_PATH_LEARNED: per-query thresholds (host or device like the queries) */
 } fps_search_opts;
 

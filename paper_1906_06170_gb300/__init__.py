@@ -19,7 +19,7 @@ _SO = os.path.join(_HERE, "libfps.so")
 FPS_BITS, FPS_WORDS, FPS_K_MAX, FPS_NOALLOC_K_MAX = 166, 3, 1920, 128
 (FPS_OK, FPS_ERR_INVALID_ARG, FPS_ERR_IO, FPS_ERR_PARSE, FPS_ERR_BUDGET, FPS_ERR_CUDA, FPS_ERR_TIMEOUT,
  FPS_ERR_OVERFLOW_INTERNAL, FPS_ERR_UNSUPPORTED, FPS_ERR_NOMEM) = range(10)
-FPS_LOAD_ACCEPT_167, FPS_LOAD_NO_BUCKETS, FPS_LOAD_TC_OPERAND = 0x1, 0x2, 0x4
+FPS_LOAD_ACCEPT_167, FPS_LOAD_NO_BUCKETS, FPS_LOAD_TC_OPERAND, FPS_LOAD_TC_INT8 = 0x1, 0x2, 0x4, 0x8
 (FPS_PATH_AUTO, FPS_PATH_POPC, FPS_PATH_POPC_BATCH, FPS_PATH_TC_FP8, FPS_PATH_TC_I8,
  FPS_PATH_LEARNED) = range(6)
 FPS_SEARCH_DEVICE_IO = 0x1
@@ -269,7 +269,7 @@ def fps_search_batch(lib: Library, queries, k, *, path: int = FPS_PATH_AUTO, out
             out_dist = torch.empty(total, dtype=torch.int32, device=dev)
         if out_count is None:
             out_count = torch.empty(max(Q, 1), dtype=torch.int32, device=dev)
-        o = _opts(path, FPS_SEARCH_DEVICE_IO, timeout_s, None, tau.data_ptr() if tau is not None else None)
+        o = _opts(path, FPS_SEARCH_DEVICE_IO, timeout_s, st_obj, tau.data_ptr() if tau is not None else None)
         st = _lib.fps_search_batch(lib._h, queries.data_ptr(), Q, kk.ctypes.data, off.ctypes.data,
                                    out_index.data_ptr(), out_dist.data_ptr(), out_count.data_ptr(), ctypes.byref(o),
                                    _stream_ptr(stream))

@@ -12,7 +12,8 @@
 //                         smallest is never below the whole set's);
 //   batch_popc_kernel     (CUDA-core popcount scan) accepts record x for query q
 //                         iff d(q, x) <= thr[q]; accepted records are counted
-//                         in hist[q] and appended to q's candidate region;
+//                         in hist[q] and appended (as distance and layout
+//                         position) to q's candidate region;
 //                         after accepting, the warp re-derives the bound (the
 //                         smallest D with >= k accepted at distance <= D) and
 //                         tightens thr[q].  Popcount buckets whose lower bound
@@ -236,9 +237,9 @@ __global__ void __launch_bounds__(256) batch_popc_kernel(DevLib lib, BatchDev b,
           if (lane == __ffs(bal) - 1) base = atomicAdd(b.cnt + q, static_cast<uint32_t>(__popc(bal)));
           base = __shfl_sync(kFull, base, __ffs(bal) - 1);
           if (acc) {
-            int32_t idx = __ldg(lib.perm + t * kTile + lane + 32 * m);
+            const uint32_t pos = static_cast<uint32_t>(t * kTile + lane + 32 * m);
             uint32_t slot = base + __popc(bal & lanemask_lt());
-            if (slot < cap) b.cand[off + slot] = (static_cast<unsigned long long>(d[m]) << 32) | static_cast<uint32_t>(idx);
+            if (slot < cap) b.cand[off + slot] = (static_cast<unsigned long long>(d[m]) << 32) | pos;
             uint32_t same = __match_any_sync(bal, d[m]);
             if ((same & lanemask_lt()) == 0) red_add_u32(hq + d[m], static_cast<uint32_t>(__popc(same)));
           }
@@ -304,7 +305,15 @@ __global__ void __launch_bounds__(kSelThreads) batch_select_kernel(DevLib lib, B
   __syncthreads();
   const uint32_t T = static_cast<uint32_t>(s_T);
   const int cless = s_cless, need = k_eff - cless;
-  const unsigned long long* cq = b.cand + off;
+  // candidate keys hold layout positions: d << 32 | position -> d << 32 | library index
+  unsigned long long* cq = b.cand + off;
+  for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+    unsigned long long key = cq[i];
+    const int32_t idx = __ldg(lib.perm + static_cast<uint32_t>(key));
+    key = (key & 0xFFFFFFFF00000000ull) | static_cast<uint32_t>(idx);
+    cq[i] = key;
+  }
+  __syncthreads();
   for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
     unsigned long long key = cq[i];
     uint32_t dd = static_cast<uint32_t>(key >> 32);

@@ -252,7 +252,10 @@ fps_status build_library(const uint64_t* packed, int64_t n, const int64_t* cids,
   const bool bucketed = !(d->flags & FPS_LOAD_NO_BUCKETS);
   std::vector<uint8_t> popc;
   Layout lay = plan_layout(packed, n, bucketed, &popc);
-  size_t need = lay.bytes;
+  const bool want_fp8 = (d->flags & FPS_LOAD_TC_OPERAND) != 0;
+  if (d->flags & FPS_LOAD_TC_INT8) return FPS_ERR_UNSUPPORTED;        // sm_103a has no tcgen05 kind::i8
+  if (want_fp8 && !bucketed) return FPS_ERR_UNSUPPORTED;              // tensor tiles need popcount buckets
+  size_t need = lay.bytes + (want_fp8 ? tc_operand_bytes(lay.n_tiles) : 0);
   if (d->hbm_budget_bytes && need > d->hbm_budget_bytes) return FPS_ERR_BUDGET;
 
   Library* L = new (std::nothrow) Library();
@@ -346,6 +349,20 @@ fps_status build_library(const uint64_t* packed, int64_t n, const int64_t* cids,
   L->dev.n = n;
   L->dev.n_tiles = lay.n_tiles;
   L->dev.bucketed = L->bucketed;
+  if (want_fp8) {
+    void* op = nullptr;
+    st = dev_alloc(L, &op, tc_operand_bytes(lay.n_tiles));
+    if (st == FPS_OK && (tc_pack_library(L->dev, static_cast<uint8_t*>(op), nullptr) != cudaSuccess ||
+                         cudaDeviceSynchronize() != cudaSuccess)) {
+      cudaGetLastError();
+      st = FPS_ERR_CUDA;
+    }
+    if (st != FPS_OK) {
+      free_library(L);
+      return st;
+    }
+    L->tc_fp8 = static_cast<uint8_t*>(op);
+  }
   *out = L;
   return FPS_OK;
 }
@@ -518,10 +535,11 @@ int64_t batch_cap(int k, int64_t n) {
 }
 
 // Many queries per launch with the batched kernels (pilot bound, scan, per-query select).
-fps_status batch_kernels(Library* L, Workspace* w, const uint64_t* queries, int Q, const int32_t* k,
+fps_status batch_kernels(Library* L, Workspace* w, int path, const uint64_t* queries, int Q, const int32_t* k,
                          const int64_t* off, int64_t total, int32_t* out_index, int32_t* out_dist,
                          int32_t* out_count, const fps_search_opts* opts, bool dev_io, cudaStream_t s,
                          int64_t* n_fallback) {
+  const bool tc = path == FPS_PATH_TC_FP8;
   std::vector<int64_t> coff(static_cast<size_t>(Q) + 1, 0);
   for (int q = 0; q < Q; ++q) coff[q + 1] = coff[q] + batch_cap(k[q], L->n);
   Carve dv;
@@ -539,6 +557,7 @@ fps_status batch_kernels(Library* L, Workspace* w, const uint64_t* queries, int 
   const size_t d_oc = dv.take(sizeof(int32_t) * Q);
   const size_t d_cand = dv.take(sizeof(unsigned long long) * static_cast<size_t>(coff[Q]));
   const size_t out_begin = dev_io ? d_oc : d_oi, out_end = d_cand;
+  const size_t d_qop = dv.take(tc ? tc_query_operand_bytes(Q) : 0);
   fps_status st = batch_staging(w, dv.at, plan_end > out_end ? plan_end : out_end);
   if (st != FPS_OK) return st;
   char* db = static_cast<char*>(w->batch_block);
@@ -565,9 +584,18 @@ fps_status batch_kernels(Library* L, Workspace* w, const uint64_t* queries, int 
   b.out_dist = dev_io ? out_dist : reinterpret_cast<int32_t*>(db + d_od);
   b.out_count = reinterpret_cast<int32_t*>(db + d_oc);
   b.err = &w->io->err;
-  if (batch_prepare(L->dev, b, 1, s) != cudaSuccess ||
-      batch_scan_popc(L->dev, b, L->num_sms, reinterpret_cast<uint32_t*>(db + d_work), s) != cudaSuccess ||
-      batch_select(L->dev, b, s) != cudaSuccess) {
+  cudaError_t ce = batch_prepare(L->dev, b, 1, s);
+  if (ce == cudaSuccess) {
+    if (tc) {
+      uint8_t* qop = reinterpret_cast<uint8_t*>(db + d_qop);
+      ce = tc_pack_queries(b.queries, Q, qop, s);
+      if (ce == cudaSuccess) ce = tc_scan(L->dev, b, L->tc_fp8, qop, L->num_sms, opt_timeout(opts), s);
+    } else {
+      ce = batch_scan_popc(L->dev, b, L->num_sms, reinterpret_cast<uint32_t*>(db + d_work), s);
+    }
+  }
+  if (ce == cudaSuccess) ce = batch_select(L->dev, b, s);
+  if (ce != cudaSuccess) {
     cudaGetLastError();
     return FPS_ERR_CUDA;
   }
@@ -629,19 +657,21 @@ fps_status search_batch_impl(Library* L, const uint64_t* queries, int Q, const i
   fps_status st = get_workspace(L, s, &w);
   if (st != FPS_OK) return st;
   const double tmo = opt_timeout(opts);
-  const int path = opts ? opts->path : FPS_PATH_AUTO;
+  int path = opts ? opts->path : FPS_PATH_AUTO;
+  if (path == FPS_PATH_AUTO) path = (L->tc_fp8 && Q >= 64) ? FPS_PATH_TC_FP8 : FPS_PATH_POPC_BATCH;
+  if (path == FPS_PATH_TC_FP8 && !L->tc_fp8) return FPS_ERR_UNSUPPORTED;
   if (path != FPS_PATH_POPC) {
-    if (path != FPS_PATH_AUTO && path != FPS_PATH_POPC_BATCH) return FPS_ERR_UNSUPPORTED;
+    if (path != FPS_PATH_POPC_BATCH && path != FPS_PATH_TC_FP8) return FPS_ERR_UNSUPPORTED;  // TC_I8: no kind::i8
     if (!dev_io)
       for (int q = 0; q < Q; ++q)
         if (queries[3 * q + 2] >> (kBits - 128)) return FPS_ERR_INVALID_ARG;
     int64_t nf = 0;
-    st = batch_kernels(L, w, queries, Q, k, off, total, out_index, out_dist, out_count, opts, dev_io, s, &nf);
+    st = batch_kernels(L, w, path, queries, Q, k, off, total, out_index, out_dist, out_count, opts, dev_io, s, &nf);
     if (st == FPS_OK && opts && opts->stats) {
       opts->stats->queries = Q;
       opts->stats->fallbacks = nf;
       opts->stats->candidates = 0;
-      opts->stats->path_used = FPS_PATH_POPC_BATCH;
+      opts->stats->path_used = path;
     }
     return st;
   }
@@ -801,7 +831,7 @@ fps_status fps_library_info_get(fps_library lib, fps_library_info* info) {
   info->device_bytes = L->device_bytes;
   info->device = L->device;
   info->bucketed = L->bucketed;
-  info->has_tc_operand = 0;
+  info->has_tc_operand = L->tc_fp8 ? 1 : 0;
   for (int b = 0; b < kNumBuckets; ++b) info->bucket_count[b] = L->bucket_count[b];
   return FPS_OK;
 }

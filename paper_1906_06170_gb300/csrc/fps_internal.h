@@ -95,6 +95,7 @@ struct Library {
   int num_sms = 0;
   std::mutex mu;
   std::map<cudaStream_t, Workspace*> ws;
+  uint8_t* tc_fp8 = nullptr;     // 0/1 FP8 operand (tensor-core path), or null
 };
 
 // Per-query state of a batched search (device pointers; fps_batch.cu).
@@ -102,7 +103,8 @@ struct Library {
 //            or from a predicted threshold, only ever tightened);
 //   hist[q]  accepted records of q per distance (168 bins, each record once);
 //   cnt[q]   candidate keys appended for q (may exceed its capacity: overflow);
-//   cand     keys d << 32 | index, query q owns [cand_off[q], cand_off[q+1]).
+//   cand     keys d << 32 | layout position (the select kernel maps positions
+//            to library indices), query q owns [cand_off[q], cand_off[q+1]).
 struct BatchDev {
   int Q;
   const uint64_t* queries;       // Q x 3 words
@@ -124,6 +126,14 @@ cudaError_t batch_prepare(const DevLib& lib, const BatchDev& b, int use_pilot, c
 cudaError_t batch_scan_popc(const DevLib& lib, const BatchDev& b, int num_sms, uint32_t* work_counter,
                             cudaStream_t s);
 cudaError_t batch_select(const DevLib& lib, const BatchDev& b, cudaStream_t s);
+
+// ---- tensor-core batched scan (fps_tc.cu)
+size_t tc_operand_bytes(int64_t n_tiles128);
+size_t tc_query_operand_bytes(int Q);
+cudaError_t tc_pack_library(const DevLib& lib, uint8_t* op, cudaStream_t s);
+cudaError_t tc_pack_queries(const uint64_t* q, int Q, uint8_t* op, cudaStream_t s);
+cudaError_t tc_scan(const DevLib& lib, const BatchDev& b, const uint8_t* lib_op, const uint8_t* q_op, int num_sms,
+                    double timeout_s, cudaStream_t s);
 
 // ---- kernels (fps_scan.cu)
 // Scan configuration chosen for a given k.

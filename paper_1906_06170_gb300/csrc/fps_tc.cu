@@ -1,0 +1,587 @@
+// Batched scan on the 5th-generation tensor cores (tcgen05, TMEM).
+//
+// Paper: Sec. 4.3 -- Manhattan distance over 166 binary keys.  For 0/1 vectors
+//   d(q, x) = sum_j |q_j - x_j| = popc(q) + popc(x) - 2 (q . x),
+// so a batch of queries against the library is one dense contraction
+// Q x K x N (K = 166 keys, padded to 192) followed by a per-element compare.
+// Operands are 0/1 bytes in FP8 E4M3 (0x38 = 1.0, 0x00 = 0) and the
+// accumulators FP32.  Every product is 0 or 1 and every sum is an integer
+// <= 166, so the accumulator is the exact integer q . x (FP32 represents all
+// integers below 2^24); the distances equal the popcount path's.  (sm_103a has
+// no tcgen05 kind::i8, so there is no INT8 variant.)
+//
+// CTA (one per SM, 6 warps):
+//   warp 0  producer: 1-D bulk copies (cp.async.bulk) of the query tile A
+//           (128 x 192 B, double-buffered per work item) and of library tiles B
+//           (256 x 192 B = 48 KB) into a 3-stage ring, completing on mbarriers;
+//   warp 1  allocates 512 TMEM columns; one thread issues 6 tcgen05.mma
+//           (kind::f8f6f4, K = 32 each) per library tile into one of two
+//           256-column FP32 accumulators and commits to the stage-free and
+//           accumulator-full barriers;
+//   warps 2..9 epilogue: thread = query (TMEM lane), two warps per lane
+//           quarter, each reading 128 of the 256 columns with tcgen05.ld (two
+//           32-column loads per wait); it takes the max per 32 columns (3-input
+//           integer max on the non-negative FP32 bit patterns) and compares it
+//           with the query's threshold on the raw accumulator,
+//             d <= thr  <=>  acc >= (popc q + popc x - thr) / 2,
+//           which needs one number per (query, tile) because a tile lies inside
+//           one popcount bucket.  Records over the bar are appended to the
+//           query's candidate region and counted in its histogram (the shared
+//           batched state of fps_batch.cu), and the bound is re-derived.
+// Operand layout (both operands, K-major, no swizzle): 8-row x 16-byte core
+// matrices of 128 contiguous bytes; along K they follow each other (leading
+// byte offset 128), along rows every 8-row group spans all 12 K-chunks (stride
+// byte offset 1536).  The library operand is written in exactly this layout at
+// load time, so a plain bulk copy lands a tile ready for the MMA.
+// Work: items (query tile, 64-tile library chunk) in chunk-major order, dealt
+// round-robin, so the 32 query tiles of a chunk run at the same time and the
+// chunk is read from HBM once and from L2 by the rest.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "fps_internal.h"
+
+namespace fps {
+namespace {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+constexpr int kTcRows = 256;                 // library records per tensor tile (N)
+constexpr int kTcQ = 128;                    // queries per CTA (M)
+constexpr int kKBytes = 192;                 // 166 keys padded to 6 x 32
+constexpr int kSbo = 1536;                   // bytes between 8-row groups
+constexpr int kLbo = 128;                    // bytes between 16-byte K chunks
+constexpr int kBTileBytes = kTcRows * kKBytes;   // 49152
+constexpr int kATileBytes = kTcQ * kKBytes;      // 24576
+constexpr int kBStages = 3;
+constexpr int kChunkTiles = 64;              // library tiles per work item
+constexpr int kEpiWarps = 8;                 // two per TMEM lane quarter, 128 columns each
+constexpr int kThreads = 32 * (2 + kEpiWarps);
+constexpr uint32_t kTmemCols = 512;
+
+// ------------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Bounded wait: gives up timeout_ns after it started (no unbounded spins).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t timeout_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t deadline = global_ns() + timeout_ns;
+  while (!mbar_try_wait(bar, parity))
+    if (global_ns() > deadline) return false;
+  return true;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: K-major, no swizzle (layout type 0).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((addr >> 4) & 0x3FFFu);
+  d |= static_cast<uint64_t>((kLbo >> 4) & 0x3FFFu) << 16;
+  d |= static_cast<uint64_t>((kSbo >> 4) & 0x3FFFu) << 32;
+  d |= 1ull << 46;  // descriptor version for tcgen05
+  return d;
+}
+
+// Instruction descriptor of kind::f8f6f4: dense, A = B = E4M3 (format 0),
+// D = F32 (format 1), both K-major, N = 256 (N >> 3 at bit 17), M = 128
+// (M >> 4 at bit 24).
+__device__ __forceinline__ uint32_t instr_desc() {
+  uint32_t d = 0;
+  d |= 1u << 4;                           // D format: F32
+  d |= 0u << 7;                           // A format: E4M3
+  d |= 0u << 10;                          // B format: E4M3
+  d |= static_cast<uint32_t>(kTcRows >> 3) << 17;
+  d |= static_cast<uint32_t>(kTcQ >> 4) << 24;
+  return d;
+}
+
+__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar))
+               : "memory");
+}
+
+// 32 consecutive TMEM columns of this thread's lane (32x32b shape); the
+// registers are valid only after tmem_wait_ld().
+__device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+        "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+        "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ void red_add_u32(uint32_t* p, uint32_t v) {
+  asm volatile("red.relaxed.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Byte offset of (row, key byte) inside a K-major no-swizzle operand tile.
+__host__ __device__ __forceinline__ uint32_t op_offset(int row, int kb) {
+  return static_cast<uint32_t>((row >> 3) * kSbo + (kb >> 4) * kLbo + (row & 7) * 16 + (kb & 15));
+}
+
+// 16 operand bytes of one record: keys 16c .. 16c+15 as 0 / one.
+__device__ __forceinline__ uint4 operand_chunk(uint64_t w0, uint64_t w1, uint64_t w2, int c, uint32_t one) {
+  uint32_t out[4];
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    uint32_t v = 0;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      int j = 16 * c + 4 * b + e;
+      uint64_t w = j < 64 ? w0 : (j < 128 ? w1 : w2);
+      uint32_t bit = (j < kBits) ? static_cast<uint32_t>((w >> (j & 63)) & 1ull) : 0u;
+      v |= (bit ? one : 0u) << (8 * e);
+    }
+    out[b] = v;
+  }
+  return make_uint4(out[0], out[1], out[2], out[3]);
+}
+
+// ------------------------------------------------------------- operand build
+// Library operand: tensor tile T covers scan tiles 2T and 2T+1 (records 256T ..).
+__global__ void tc_pack_library_kernel(DevLib lib, uint8_t* op, int64_t n_tc, uint32_t one) {
+  const int64_t total = n_tc * kTcRows * (kKBytes / 16);
+  for (int64_t u = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; u < total;
+       u += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    int64_t T = u / (kTcRows * 12);
+    int rem = static_cast<int>(u % (kTcRows * 12));
+    int g = rem / 96, rr = (rem % 96) % 8, c = (rem % 96) / 8;
+    int row = 8 * g + rr;
+    int64_t pos = T * kTcRows + row;
+    const uint64_t* w = lib.words + (pos / kTile) * (kWords * kTile) + (pos % kTile);
+    uint4 v = operand_chunk(w[0], w[kTile], w[2 * kTile], c, one);
+    *reinterpret_cast<uint4*>(op + T * kBTileBytes + op_offset(row, 16 * c)) = v;
+  }
+}
+
+// Query operand: Q rounded up to 128-row tiles, rows past Q are zero.
+__global__ void tc_pack_queries_kernel(const uint64_t* q, int Q, uint8_t* op, int q_tiles, uint32_t one) {
+  const int total = q_tiles * kTcQ * 12;
+  for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < total; u += gridDim.x * blockDim.x) {
+    int t = u / (kTcQ * 12), rem = u % (kTcQ * 12);
+    int g = rem / 96, rr = (rem % 96) % 8, c = (rem % 96) / 8;
+    int row = 8 * g + rr, qi = t * kTcQ + row;
+    uint4 v = make_uint4(0, 0, 0, 0);
+    if (qi < Q) v = operand_chunk(q[3 * qi], q[3 * qi + 1], q[3 * qi + 2], c, one);
+    *reinterpret_cast<uint4*>(op + static_cast<size_t>(t) * kATileBytes + op_offset(row, 16 * c)) = v;
+  }
+}
+
+// ------------------------------------------------------------------- scan
+struct TcSmem {
+  uint8_t a[2][kATileBytes];
+  uint8_t b[kBStages][kBTileBytes];
+  uint64_t b_full[kBStages], b_empty[kBStages];
+  uint64_t a_full[2], a_empty[2];
+  uint64_t acc_full[2], acc_empty[2];
+  uint64_t fin;
+  uint32_t tmem_base;
+  int tile_off2[kNumBuckets + 1];  // first tensor tile of each bucket
+  int bcount[kNumBuckets + 1];
+};
+
+// Smallest D <= thr with at least k counts in hist[0..D], else 167.  The first
+// 48 bins are fetched in one round trip; larger bounds continue 8 bins at a time.
+__device__ __forceinline__ uint32_t bound_of(const uint32_t* hist, uint32_t thr, int k) {
+  uint32_t run = 0;
+  uint32_t h[48];
+#pragma unroll
+  for (int e = 0; e < 48; e += 2) {
+    uint2 v = __ldcg(reinterpret_cast<const uint2*>(hist + e));
+    h[e] = v.x;
+    h[e + 1] = v.y;
+  }
+#pragma unroll
+  for (int e = 0; e < 48; ++e) {
+    if (static_cast<uint32_t>(e) > thr) return 167u;
+    run += h[e];
+    if (run >= static_cast<uint32_t>(k)) return static_cast<uint32_t>(e);
+  }
+  for (uint32_t base = 48; base <= thr; base += 8) {
+    uint32_t h8[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) h8[e] = (base + e <= thr) ? __ldcg(hist + base + e) : 0u;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      if (base + e > thr) return 167u;
+      run += h8[e];
+      if (run >= static_cast<uint32_t>(k)) return base + e;
+    }
+  }
+  return 167u;
+}
+
+// Bucket of tensor tile T (tiles of one bucket are contiguous).
+__device__ __forceinline__ int bucket_of(const int* off2, int64_t T) {
+  int lo = 0, hi = kNumBuckets - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (off2[mid] <= T)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    tc_scan_kernel(DevLib lib, BatchDev b, const uint8_t* __restrict__ lib_op, const uint8_t* __restrict__ q_op,
+                   int64_t n_tc, int n_qt, uint64_t timeout_ns) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  TcSmem& S = *reinterpret_cast<TcSmem*>(smem_raw);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t n_chunks = (n_tc + kChunkTiles - 1) / kChunkTiles;
+  const int64_t n_items = n_chunks * n_qt;
+
+  for (int i = threadIdx.x; i < kNumBuckets + 1; i += blockDim.x) {
+    S.tile_off2[i] = lib.tile_off[i] / 2;
+    S.bcount[i] = i < kNumBuckets ? lib.bcount[i] : 0;
+  }
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kBStages; ++s) {
+      mbar_init(&S.b_full[s], 1);
+      mbar_init(&S.b_empty[s], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&S.a_full[i], 1);
+      mbar_init(&S.a_empty[i], 1);
+      mbar_init(&S.acc_full[i], 1);
+      mbar_init(&S.acc_empty[i], kEpiWarps);
+    }
+    mbar_init(&S.fin, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&S.tmem_base)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = S.tmem_base;
+  const uint64_t deadline = timeout_ns;   // per wait
+  bool ok = true;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------- producer
+    if (lane == 0) {
+      uint32_t bn = 0;  // library tiles issued so far
+      uint32_t na = 0;  // query tiles issued so far
+      for (int64_t j = 0; ok; ++j) {
+        const int64_t item = blockIdx.x + j * gridDim.x;
+        if (item >= n_items) break;
+        const int qt = static_cast<int>(item % n_qt);
+        const int64_t c = item / n_qt;
+        const int ab = static_cast<int>(j & 1);
+        if (!mbar_wait(&S.a_empty[ab], static_cast<uint32_t>(((j >> 1) & 1) ^ 1), deadline)) {
+          ok = false;
+          break;
+        }
+        mbar_arrive_expect_tx(&S.a_full[ab], kATileBytes);
+        bulk_g2s(S.a[ab], q_op + static_cast<size_t>(qt) * kATileBytes, kATileBytes, &S.a_full[ab]);
+        ++na;
+        const int64_t t0 = c * kChunkTiles, t1 = min(t0 + kChunkTiles, n_tc);
+        for (int64_t T = t0; T < t1; ++T, ++bn) {
+          const int s = static_cast<int>(bn % kBStages);
+          const uint32_t use = bn / kBStages;
+          if (!mbar_wait(&S.b_empty[s], (use & 1) ^ 1, deadline)) {
+            ok = false;
+            break;
+          }
+          mbar_arrive_expect_tx(&S.b_full[s], kBTileBytes);
+          const uint8_t* src = lib_op + T * kBTileBytes;
+#pragma unroll
+          for (int part = 0; part < 3; ++part)
+            bulk_g2s(S.b[s] + part * (kBTileBytes / 3), src + part * (kBTileBytes / 3), kBTileBytes / 3, &S.b_full[s]);
+        }
+      }
+      // wait (bounded) for copies still in flight before anyone leaves
+      for (int s = 0; s < kBStages; ++s) {
+        if (bn > static_cast<uint32_t>(s)) {
+          uint32_t last_use = (bn - 1 - s) / kBStages;
+          mbar_wait(&S.b_full[s], last_use & 1, timeout_ns);
+        }
+      }
+      for (int a = 0; a < 2; ++a) {
+        if (na > static_cast<uint32_t>(a)) {
+          uint32_t last_use = (na - 1 - a) / 2;
+          mbar_wait(&S.a_full[a], last_use & 1, timeout_ns);
+        }
+      }
+      if (!ok) atomicOr(b.err, DEVERR_TIMEOUT);
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issue
+    if (lane == 0) {
+      const uint32_t idesc = instr_desc();
+      uint32_t bn = 0, tn = 0;  // library tiles consumed, accumulators produced
+      for (int64_t j = 0; ok; ++j) {
+        const int64_t item = blockIdx.x + j * gridDim.x;
+        if (item >= n_items) break;
+        const int64_t c = item / n_qt;
+        const int ab = static_cast<int>(j & 1);
+        if (!mbar_wait(&S.a_full[ab], static_cast<uint32_t>((j >> 1) & 1), deadline)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t a_base = smem_addr(S.a[ab]);
+        const int64_t t0 = c * kChunkTiles, t1 = min(t0 + kChunkTiles, n_tc);
+        for (int64_t T = t0; T < t1; ++T, ++bn, ++tn) {
+          const int s = static_cast<int>(bn % kBStages);
+          const int acc = static_cast<int>(tn & 1);
+          if (!mbar_wait(&S.acc_empty[acc], ((tn >> 1) & 1) ^ 1, deadline) ||
+              !mbar_wait(&S.b_full[s], (bn / kBStages) & 1, deadline)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t b_base = smem_addr(S.b[s]);
+          const uint32_t d_tmem = tmem + static_cast<uint32_t>(acc * kTcRows);
+#pragma unroll
+          for (int ks = 0; ks < kKBytes / 32; ++ks)
+            mma(d_tmem, smem_desc(a_base + 256 * ks), smem_desc(b_base + 256 * ks), idesc, ks > 0 ? 1u : 0u);
+          mma_commit(&S.b_empty[s]);
+          mma_commit(&S.acc_full[acc]);
+        }
+        if (!ok) break;
+        mma_commit(&S.a_empty[ab]);
+      }
+      if (!ok) atomicOr(b.err, DEVERR_TIMEOUT);
+      // all MMAs issued by this thread complete before the final barrier
+      mma_commit(&S.fin);
+      mbar_wait(&S.fin, 0, timeout_ns);
+    }
+  } else {
+    // -------------------------------------------------------------- epilogue
+    const int ew = warp - 2;
+    const int quarter = warp & 3;                 // TMEM lanes 32*quarter .. +31
+    const int half = ew >> 2;                     // columns 128*half .. +127
+    const int row = 32 * quarter + lane;          // query row inside the tile
+    const uint32_t lane_addr = static_cast<uint32_t>(32 * quarter) << 16;
+    uint32_t tn = 0;
+    int bk = 0;                                   // bucket cursor (tiles arrive in ascending order per item)
+    for (int64_t j = 0; ok; ++j) {
+      const int64_t item = blockIdx.x + j * gridDim.x;
+      if (item >= n_items) break;
+      const int qt = static_cast<int>(item % n_qt);
+      const int64_t c = item / n_qt;
+      const int q = qt * kTcQ + row;
+      const bool live = q < b.Q && b.k[q] > 0;
+      const int kq = live ? b.k[q] : 0;
+      int pq = 0;
+      uint32_t thr = 0;
+      int64_t coff = 0, ccap = 0;
+      uint32_t* hq = nullptr;
+      if (live) {
+        pq = __popcll(b.queries[3 * q]) + __popcll(b.queries[3 * q + 1]) + __popcll(b.queries[3 * q + 2]);
+        thr = ld_relaxed_u32(b.thr + q);
+        coff = b.cand_off[q];
+        ccap = b.cand_off[q + 1] - coff;
+        hq = b.hist + static_cast<size_t>(q) * 168;
+      }
+      uint32_t pending = 0;                        // accepted since the last bound refresh
+      const uint32_t refresh_at = 4u;
+      bool refresh = false;                        // histogram bins requested for this tile
+      uint32_t hb[48];
+      const int64_t t0 = c * kChunkTiles, t1 = min(t0 + kChunkTiles, n_tc);
+      bk = bucket_of(S.tile_off2, t0);
+      for (int64_t T = t0; T < t1; ++T, ++tn) {
+        const int acc = static_cast<int>(tn & 1);
+        while (bk + 1 < kNumBuckets && S.tile_off2[bk + 1] <= T) ++bk;
+        int nvalid = S.bcount[bk] - static_cast<int>(T - S.tile_off2[bk]) * kTcRows;
+        nvalid = nvalid < kTcRows ? nvalid : kTcRows;
+        const bool act = live && static_cast<uint32_t>(abs(bk - pq)) <= thr;
+        // acc >= (pq + px - thr) / 2  <=>  d <= thr;  twice the bar keeps it an integer
+        const int bar2 = pq + bk - static_cast<int>(thr);
+        if (refresh) {
+          // issue the histogram loads now; they are consumed after this tile's work
+#pragma unroll
+          for (int e = 0; e < 48; e += 2) {
+            uint2 v = __ldcg(reinterpret_cast<const uint2*>(hq + e));
+            hb[e] = v.x;
+            hb[e + 1] = v.y;
+          }
+        }
+        const bool landed = mbar_wait(&S.acc_full[acc], (tn >> 1) & 1, deadline);
+        if (!__all_sync(kFull, landed)) {   // one verdict for the whole warp
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        if (__any_sync(kFull, act)) {
+          for (int ch = 0; ch < 4; ch += 2) {
+            uint32_t v[2][32];
+            const uint32_t col0 = static_cast<uint32_t>(acc * kTcRows + half * 128 + ch * 32);
+            __syncwarp();   // warp-collective loads: reconverge lanes that skipped the previous chunk
+            tmem_ld32_nowait(tmem + lane_addr + col0, v[0]);
+            tmem_ld32_nowait(tmem + lane_addr + col0 + 32, v[1]);
+            tmem_wait_ld();
+            if (!act) continue;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              // FP32 values here are non-negative integers: their bit patterns order like ints
+              int m = __vimax3_s32(static_cast<int>(v[h][0]), static_cast<int>(v[h][1]), static_cast<int>(v[h][2]));
+#pragma unroll
+              for (int e = 3; e < 31; e += 2) m = __vimax3_s32(m, static_cast<int>(v[h][e]), static_cast<int>(v[h][e + 1]));
+              m = max(m, static_cast<int>(v[h][31]));
+              if (2 * static_cast<int>(__int_as_float(m)) < bar2) continue;
+              // rare: some record of these 32 is within the bound
+#pragma unroll
+              for (int e = 0; e < 32; ++e) {
+                const int a = static_cast<int>(__uint_as_float(v[h][e]));
+                const int col = half * 128 + (ch + h) * 32 + e;
+                if (2 * a < bar2 || col >= nvalid) continue;
+                const uint32_t d = static_cast<uint32_t>(pq + bk - 2 * a);
+                // key by layout position; the select kernel maps positions to indices
+                const uint32_t pos = static_cast<uint32_t>(T * kTcRows + col);
+                const uint32_t slot = atomicAdd(b.cnt + q, 1u);
+                if (slot < ccap) b.cand[coff + slot] = (static_cast<unsigned long long>(d) << 32) | pos;
+                red_add_u32(hq + d, 1u);
+                ++pending;
+              }
+            }
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&S.acc_empty[acc]);
+        // tighten this query's bound from the bins fetched during this tile
+        if (refresh) {
+          refresh = false;
+          uint32_t run = 0, D = 167u;
+#pragma unroll
+          for (int e = 0; e < 48; ++e) {
+            run += hb[e];
+            if (D == 167u && run >= static_cast<uint32_t>(kq) && static_cast<uint32_t>(e) <= thr) D = e;
+          }
+          if (D < thr) {
+            thr = D;
+            atomicMin(b.thr + q, D);
+          }
+        }
+        if (live && pending >= refresh_at) {   // request a refresh for the next tile
+          pending = 0;
+          refresh = true;
+        }
+        if (live && ((T - t0) & 15) == 15) {
+          uint32_t g = ld_relaxed_u32(b.thr + q);
+          thr = g < thr ? g : thr;
+        }
+      }
+      if (live) {
+        if (pending > 0 || refresh) {  // the next item is another query tile: refresh now
+          const uint32_t D = bound_of(hq, thr, kq);
+          if (D < thr) atomicMin(b.thr + q, D);
+        }
+      }
+      if (!ok) break;
+    }
+    if (!ok && lane == 0) atomicOr(b.err, DEVERR_TIMEOUT);
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+}
+
+cudaError_t launch_tc(const DevLib& lib, const BatchDev& b, const uint8_t* lib_op, const uint8_t* q_op, int64_t n_tc,
+                      int n_qt, int num_sms, double timeout_s, cudaStream_t s) {
+  const size_t smem = sizeof(TcSmem) + 1024;
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(tc_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  const uint64_t tns = static_cast<uint64_t>((timeout_s > 0 ? timeout_s : 2.0) * 1e9);
+  tc_scan_kernel<<<num_sms, kThreads, smem, s>>>(lib, b, lib_op, q_op, n_tc, n_qt, tns);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t tc_operand_bytes(int64_t n_tiles128) { return static_cast<size_t>((n_tiles128 + 1) / 2) * kBTileBytes; }
+size_t tc_query_operand_bytes(int Q) { return static_cast<size_t>((Q + kTcQ - 1) / kTcQ) * kATileBytes; }
+
+cudaError_t tc_pack_library(const DevLib& lib, uint8_t* op, cudaStream_t s) {
+  const int64_t n_tc = (lib.n_tiles + 1) / 2;
+  if (n_tc == 0) return cudaSuccess;
+  tc_pack_library_kernel<<<4096, 256, 0, s>>>(lib, op, n_tc, 0x38u);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_pack_queries(const uint64_t* q, int Q, uint8_t* op, cudaStream_t s) {
+  const int q_tiles = (Q + kTcQ - 1) / kTcQ;
+  if (q_tiles == 0) return cudaSuccess;
+  const int total = q_tiles * kTcQ * 12;
+  tc_pack_queries_kernel<<<(total + 255) / 256, 256, 0, s>>>(q, Q, op, q_tiles, 0x38u);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_scan(const DevLib& lib, const BatchDev& b, const uint8_t* lib_op, const uint8_t* q_op, int num_sms,
+                    double timeout_s, cudaStream_t s) {
+  const int64_t n_tc = (lib.n_tiles + 1) / 2;
+  const int n_qt = (b.Q + kTcQ - 1) / kTcQ;
+  if (n_tc == 0 || n_qt == 0) return cudaSuccess;
+  return launch_tc(lib, b, lib_op, q_op, n_tc, n_qt, num_sms, timeout_s, s);
+}
+
+}  // namespace fps

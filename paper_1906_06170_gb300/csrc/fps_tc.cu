@@ -18,6 +18,9 @@
 //           (kind::f8f6f4, K = 32 each) per library tile into one of two
 //           256-column FP32 accumulators and commits to the stage-free and
 //           accumulator-full barriers;
+//   warp 10 drains the CTA's queue of accepted records into the per-query
+//           candidate regions (32 returning atomics per round trip), so the
+//           epilogue never waits on a global atomic;
 //   warps 2..9 epilogue: thread = query (TMEM lane), two warps per lane
 //           quarter, each reading 128 of the 256 columns with tcgen05.ld (two
 //           32-column loads per wait); it takes the max per 32 columns (3-input
@@ -56,7 +59,9 @@ constexpr int kATileBytes = kTcQ * kKBytes;      // 24576
 constexpr int kBStages = 3;
 constexpr int kChunkTiles = 64;              // library tiles per work item
 constexpr int kEpiWarps = 8;                 // two per TMEM lane quarter, 128 columns each
-constexpr int kThreads = 32 * (2 + kEpiWarps);
+constexpr int kFlushWarp = 2 + kEpiWarps;    // drains the candidate queue
+constexpr int kThreads = 32 * (3 + kEpiWarps);
+constexpr uint32_t kQueueCap = 1024;         // accepted records in flight per CTA
 constexpr uint32_t kTmemCols = 512;
 
 // ------------------------------------------------------------------ PTX helpers
@@ -220,6 +225,11 @@ __global__ void tc_pack_queries_kernel(const uint64_t* q, int Q, uint8_t* op, in
 }
 
 // ------------------------------------------------------------------- scan
+// Accepted record waiting for the flusher; seq = queue slot + 1 once written.
+struct QEntry {
+  uint32_t q, d, pos, seq;
+};
+
 struct TcSmem {
   uint8_t a[2][kATileBytes];
   uint8_t b[kBStages][kBTileBytes];
@@ -230,7 +240,29 @@ struct TcSmem {
   uint32_t tmem_base;
   int tile_off2[kNumBuckets + 1];  // first tensor tile of each bucket
   int bcount[kNumBuckets + 1];
+  QEntry queue[kQueueCap];
+  uint32_t q_tail;                 // slots claimed by the epilogue
+  uint32_t q_head;                 // slots retired by the flusher
+  uint32_t epi_done;               // epilogue warps finished
 };
+
+// Epilogue side: claim a queue slot, wait (bounded) for room, write the entry.
+// Out of line: it runs rarely and must not bloat the unrolled accumulator scan.
+__device__ __noinline__ bool queue_push(TcSmem& S, uint32_t q, uint32_t d, uint32_t pos, uint64_t timeout_ns) {
+  const uint32_t slot = atomicAdd(&S.q_tail, 1u);
+  if (slot - *reinterpret_cast<volatile uint32_t*>(&S.q_head) >= kQueueCap) {
+    const uint64_t deadline = global_ns() + timeout_ns;
+    while (slot - *reinterpret_cast<volatile uint32_t*>(&S.q_head) >= kQueueCap)
+      if (global_ns() > deadline) return false;
+  }
+  QEntry& e = S.queue[slot % kQueueCap];
+  e.q = q;
+  e.d = d;
+  e.pos = pos;
+  __threadfence_block();
+  *reinterpret_cast<volatile uint32_t*>(&e.seq) = slot + 1;
+  return true;
+}
 
 // Smallest D <= thr with at least k counts in hist[0..D], else 167.  The first
 // 48 bins are fetched in one round trip; larger bounds continue 8 bins at a time.
@@ -301,8 +333,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&S.acc_empty[i], kEpiWarps);
     }
     mbar_init(&S.fin, 1);
+    S.q_tail = 0;
+    S.q_head = 0;
+    S.epi_done = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  for (uint32_t i = threadIdx.x; i < kQueueCap; i += blockDim.x) S.queue[i].seq = 0;
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&S.tmem_base)),
                  "r"(kTmemCols)
@@ -406,7 +442,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       mma_commit(&S.fin);
       mbar_wait(&S.fin, 0, timeout_ns);
     }
-  } else {
+  } else if (warp < kFlushWarp) {
     // -------------------------------------------------------------- epilogue
     const int ew = warp - 2;
     const int quarter = warp & 3;                 // TMEM lanes 32*quarter .. +31
@@ -425,13 +461,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int kq = live ? b.k[q] : 0;
       int pq = 0;
       uint32_t thr = 0;
-      int64_t coff = 0, ccap = 0;
       uint32_t* hq = nullptr;
       if (live) {
         pq = __popcll(b.queries[3 * q]) + __popcll(b.queries[3 * q + 1]) + __popcll(b.queries[3 * q + 2]);
         thr = ld_relaxed_u32(b.thr + q);
-        coff = b.cand_off[q];
-        ccap = b.cand_off[q + 1] - coff;
         hq = b.hist + static_cast<size_t>(q) * 168;
       }
       uint32_t pending = 0;                        // accepted since the last bound refresh
@@ -448,6 +481,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const bool act = live && static_cast<uint32_t>(abs(bk - pq)) <= thr;
         // acc >= (pq + px - thr) / 2  <=>  d <= thr;  twice the bar keeps it an integer
         const int bar2 = pq + bk - static_cast<int>(thr);
+        if (live && pending > 0 && T + 1 == t1) refresh = true;   // last tile: refresh before the query tile changes
         if (refresh) {
           // issue the histogram loads now; they are consumed after this tile's work
 #pragma unroll
@@ -480,18 +514,26 @@ __global__ void __launch_bounds__(kThreads, 1)
               for (int e = 3; e < 31; e += 2) m = __vimax3_s32(m, static_cast<int>(v[h][e]), static_cast<int>(v[h][e + 1]));
               m = max(m, static_cast<int>(v[h][31]));
               if (2 * static_cast<int>(__int_as_float(m)) < bar2) continue;
-              // rare: some record of these 32 is within the bound
+              // rare: some record of these 32 is within the bound.  Mark the passing
+              // columns, then take them one by one (a select chain reads v[e] without
+              // indexing registers dynamically).
+              const int colb = half * 128 + (ch + h) * 32;
+              uint32_t mask = 0;
 #pragma unroll
-              for (int e = 0; e < 32; ++e) {
-                const int a = static_cast<int>(__uint_as_float(v[h][e]));
-                const int col = half * 128 + (ch + h) * 32 + e;
-                if (2 * a < bar2 || col >= nvalid) continue;
+              for (int e = 0; e < 32; ++e)
+                mask |= static_cast<uint32_t>(2 * static_cast<int>(__uint_as_float(v[h][e])) >= bar2 &&
+                                              colb + e < nvalid) << e;
+              while (mask) {
+                const int e0 = __ffs(mask) - 1;
+                mask &= mask - 1;
+                uint32_t raw = 0;
+#pragma unroll
+                for (int e = 0; e < 32; ++e) raw = (e == e0) ? v[h][e] : raw;
+                const int a = static_cast<int>(__uint_as_float(raw));
                 const uint32_t d = static_cast<uint32_t>(pq + bk - 2 * a);
-                // key by layout position; the select kernel maps positions to indices
-                const uint32_t pos = static_cast<uint32_t>(T * kTcRows + col);
-                const uint32_t slot = atomicAdd(b.cnt + q, 1u);
-                if (slot < ccap) b.cand[coff + slot] = (static_cast<unsigned long long>(d) << 32) | pos;
+                const uint32_t pos = static_cast<uint32_t>(T * kTcRows + colb + e0);
                 red_add_u32(hq + d, 1u);
+                if (!queue_push(S, static_cast<uint32_t>(q), d, pos, deadline)) ok = false;
                 ++pending;
               }
             }
@@ -523,15 +565,50 @@ __global__ void __launch_bounds__(kThreads, 1)
           thr = g < thr ? g : thr;
         }
       }
-      if (live) {
-        if (pending > 0 || refresh) {  // the next item is another query tile: refresh now
-          const uint32_t D = bound_of(hq, thr, kq);
-          if (D < thr) atomicMin(b.thr + q, D);
-        }
+      if (live && refresh) {  // a refresh was due at the item's end: do it before the query tile changes
+        const uint32_t D = bound_of(hq, thr, kq);
+        if (D < thr) atomicMin(b.thr + q, D);
       }
       if (!ok) break;
     }
     if (!ok && lane == 0) atomicOr(b.err, DEVERR_TIMEOUT);
+    __syncwarp();
+    if (lane == 0) atomicAdd(&S.epi_done, 1u);
+  } else if (warp == kFlushWarp) {
+    // ---------------------------------------------------------------- flusher
+    uint32_t head = 0;
+    uint64_t idle_since = 0;
+    for (;;) {
+      const uint32_t idx = head + lane;
+      const bool ready = *reinterpret_cast<volatile uint32_t*>(&S.queue[idx % kQueueCap].seq) == idx + 1;
+      const uint32_t bal = __ballot_sync(kFull, ready);
+      const int n = bal == kFull ? 32 : __ffs(~bal) - 1;   // ready entries in a row from head
+      if (n == 0) {
+        const bool epi_over = *reinterpret_cast<volatile uint32_t*>(&S.epi_done) == kEpiWarps;
+        if (epi_over && *reinterpret_cast<volatile uint32_t*>(&S.q_tail) == head) break;
+        // idle: wait for the epilogue (itself bounded); claimed-but-unwritten slots after
+        // it finished get timeout_ns, and no idle spell may exceed 32 x timeout_ns
+        const uint64_t now = global_ns();
+        if (idle_since == 0) idle_since = now;
+        if (now - idle_since > (epi_over ? timeout_ns : 32 * timeout_ns)) {
+          if (lane == 0) atomicOr(b.err, DEVERR_TIMEOUT);
+          break;
+        }
+        __nanosleep(256);
+        continue;
+      }
+      idle_since = 0;
+      __threadfence_block();
+      if (lane < n) {
+        const QEntry& e = S.queue[idx % kQueueCap];
+        const int64_t off = b.cand_off[e.q], cap = b.cand_off[e.q + 1] - off;
+        const uint32_t slot = atomicAdd(b.cnt + e.q, 1u);
+        if (slot < cap) b.cand[off + slot] = (static_cast<unsigned long long>(e.d) << 32) | e.pos;
+      }
+      __syncwarp();
+      head += n;
+      if (lane == 0) *reinterpret_cast<volatile uint32_t*>(&S.q_head) = head;
+    }
   }
 
   tc_fence_before();

@@ -137,7 +137,7 @@ typedef enum {
 typedef struct {
   int64_t queries;               /* queries served by the call */
   int64_t fallbacks;             /* queries that needed the exact fallback scan */
-  int64_t candidates;            /* candidate keys examined by the final selection */
+  int64_t candidates;            /* records accepted under the running bounds (batched paths) */
   int64_t path_used;             /* fps_path actually run */
 } fps_search_stats;
 
@@ -146,7 +146,8 @@ typedef struct {
   uint32_t flags;                /* FPS_SEARCH_* */
   double timeout_s;              /* bound on any device-side wait; <= 0 = 2 s */
   fps_search_stats* stats;       /* optional out (host memory; filled by fps_search_batch in both forms) */
-  const float* tau;              /* FPS_PATH_LEARNED: per-query thresholds (host or device like the queries) */
+  const float* tau;              /* FPS_PATH_LEARNED: per-query predicted k-th distances (host or device like
+                                    the queries); the scan starts from bound ceil(tau), clamped to 0..166 */
 } fps_search_opts;
 
 /*
@@ -209,6 +210,39 @@ fps_status fps_search_noalloc(fps_library lib, const uint64_t* query, int k, int
 
 /* Wait for cuda_stream and report (then clear) any device-side error of searches enqueued on it. */
 fps_status fps_sync(fps_library lib, void* cuda_stream);
+
+/* ---------------------------------------------------- learned threshold (MLP)
+ *
+ * The paper has no counterpart: this small network predicts a query's k-th
+ * nearest distance so the batched scan (FPS_PATH_LEARNED) can start from a
+ * tight per-query bound instead of the sampled one.  Results stay exact: a
+ * query whose prediction was too low (fewer than k records at or under it) is
+ * re-run by the exact scan.
+ *   x  = [166 query bits, popc(q)/166];  h1 = relu(W1 x + b1)  (256);
+ *   h2 = relu(W2 h1 + b2) (256);  y = w3 . h2 + b3.
+ * BF16 weights in every product (FP32 masters for Adam), FP32 accumulation,
+ * mean pinball loss at a chosen quantile.  Parameters are one flat FP32 array
+ * in the order W1 (256 x 167, row-major), b1, W2 (256 x 256), b2, w3, b3.
+ */
+typedef struct fps_mlp_s* fps_mlp;
+
+/* Number of FP32 parameters (109057). */
+size_t fps_mlp_param_count(void);
+/* A model on `device` with all parameters zero (set them with fps_mlp_set_params). */
+fps_status fps_mlp_create(int device, fps_mlp* out);
+fps_status fps_mlp_release(fps_mlp mlp);
+/* Copy parameters in (resets the Adam moments and step) / out; host arrays of fps_mlp_param_count() floats. */
+fps_status fps_mlp_set_params(fps_mlp mlp, const float* host, size_t n);
+fps_status fps_mlp_get_params(fps_mlp mlp, float* host, size_t n);
+/* Predicted thresholds for Q packed queries; queries and out are device pointers; asynchronous on the stream. */
+fps_status fps_mlp_predict(fps_mlp mlp, const uint64_t* queries, int Q, float* out, void* cuda_stream);
+/* Forward + backward on B examples (device queries and targets); gradients stay on the device and are copied
+   to grad_host (fps_mlp_param_count() floats) and the mean loss to loss_host when those are non-NULL. */
+fps_status fps_mlp_grad(fps_mlp mlp, const uint64_t* queries, const float* targets, int B, float quantile,
+                        float* grad_host, float* loss_host, void* cuda_stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on B examples; loss_host (nullable) gets the mean loss. */
+fps_status fps_mlp_train_step(fps_mlp mlp, const uint64_t* queries, const float* targets, int B, float quantile,
+                              float lr, float* loss_host, void* cuda_stream);
 
 /* ----------------------------------------------------------------- helpers */
 

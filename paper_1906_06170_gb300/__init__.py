@@ -72,11 +72,21 @@ _lib.fps_search_packed.argtypes = [_vp, _vp, _i32, _vp, _vp, _vp, ctypes.POINTER
 _lib.fps_search_batch.argtypes = [_vp, _vp, _i32, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(fps_search_opts), _vp]
 _lib.fps_sync.argtypes = [_vp, _vp]
 _lib.fps_search_noalloc.argtypes = [_vp, _vp, _i32, _vp, _vp, _vp, _vp]
+_lib.fps_mlp_param_count.restype = ctypes.c_size_t
+_lib.fps_mlp_create.argtypes = [_i32, ctypes.POINTER(_vp)]
+_lib.fps_mlp_release.argtypes = [_vp]
+_lib.fps_mlp_set_params.argtypes = [_vp, _vp, ctypes.c_size_t]
+_lib.fps_mlp_get_params.argtypes = [_vp, _vp, ctypes.c_size_t]
+_lib.fps_mlp_predict.argtypes = [_vp, _vp, _i32, _vp, _vp]
+_lib.fps_mlp_grad.argtypes = [_vp, _vp, _vp, _i32, ctypes.c_float, _vp, _vp, _vp]
+_lib.fps_mlp_train_step.argtypes = [_vp, _vp, _vp, _i32, ctypes.c_float, ctypes.c_float, _vp, _vp]
 _lib.fps_pack_query.argtypes = [ctypes.c_char_p, _vp]
 _lib.fps_pack_text.argtypes = [_vp, ctypes.c_size_t, ctypes.c_uint32, _vp, _vp, ctypes.c_size_t,
                                ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]
 for _f in ("fps_library_load", "fps_release", "fps_library_info_get", "fps_library_cid", "fps_search",
-           "fps_search_packed", "fps_search_batch", "fps_sync", "fps_pack_query", "fps_pack_text", "fps_search_noalloc"):
+           "fps_search_packed", "fps_search_batch", "fps_sync", "fps_pack_query", "fps_pack_text", "fps_search_noalloc",
+           "fps_mlp_create", "fps_mlp_release", "fps_mlp_set_params", "fps_mlp_get_params", "fps_mlp_predict",
+           "fps_mlp_grad", "fps_mlp_train_step"):
     getattr(_lib, _f).restype = _i32
 
 
@@ -330,3 +340,72 @@ def fps_pack_text(text, flags: int = 0):
                             ctypes.byref(err))
     _check(st, "fps_pack_text", err.value)
     return packed[: n.value], cids[: n.value]
+
+
+# ------------------------------------------------------------ learned threshold MLP
+class Mlp:
+    """Threshold-predicting MLP handle (device weights)."""
+
+    def __init__(self, handle: int):
+        self.handle = handle
+
+    @property
+    def _h(self):
+        if not self.handle:
+            raise FpsError(FPS_ERR_INVALID_ARG, "released model")
+        return self.handle
+
+
+def fps_mlp_param_count() -> int:
+    return int(_lib.fps_mlp_param_count())
+
+
+def fps_mlp_create(device: int = 0) -> Mlp:
+    h = _vp()
+    _check(_lib.fps_mlp_create(device, ctypes.byref(h)), "fps_mlp_create")
+    return Mlp(h.value)
+
+
+def fps_mlp_release(m: Mlp):
+    if m is not None and m.handle:
+        _check(_lib.fps_mlp_release(m.handle), "fps_mlp_release")
+        m.handle = None
+
+
+def fps_mlp_set_params(m: Mlp, params) -> None:
+    p = np.ascontiguousarray(np.asarray(params, dtype=np.float32).reshape(-1))
+    _check(_lib.fps_mlp_set_params(m._h, p.ctypes.data, p.size), "fps_mlp_set_params")
+
+
+def fps_mlp_get_params(m: Mlp) -> np.ndarray:
+    p = np.zeros(fps_mlp_param_count(), np.float32)
+    _check(_lib.fps_mlp_get_params(m._h, p.ctypes.data, p.size), "fps_mlp_get_params")
+    return p
+
+
+def fps_mlp_predict(m: Mlp, queries, out=None, stream=None):
+    """queries: CUDA int64/uint64 tensor [Q, 3]; returns a CUDA float32 tensor [Q] (asynchronous)."""
+    import torch
+
+    Q = int(queries.shape[0])
+    if out is None:
+        out = torch.empty(max(Q, 1), dtype=torch.float32, device=queries.device)
+    _check(_lib.fps_mlp_predict(m._h, queries.data_ptr(), Q, out.data_ptr(), _stream_ptr(stream)), "fps_mlp_predict")
+    return out
+
+
+def fps_mlp_grad(m: Mlp, queries, targets, quantile: float, stream=None):
+    """(mean loss, flat FP32 gradient) for device queries [B, 3] and targets [B]."""
+    g = np.zeros(fps_mlp_param_count(), np.float32)
+    loss = np.zeros(1, np.float32)
+    _check(_lib.fps_mlp_grad(m._h, queries.data_ptr(), targets.data_ptr(), int(queries.shape[0]), float(quantile),
+                             g.ctypes.data, loss.ctypes.data, _stream_ptr(stream)), "fps_mlp_grad")
+    return float(loss[0]), g
+
+
+def fps_mlp_train_step(m: Mlp, queries, targets, quantile: float, lr: float, want_loss: bool = False, stream=None):
+    loss = np.zeros(1, np.float32)
+    _check(_lib.fps_mlp_train_step(m._h, queries.data_ptr(), targets.data_ptr(), int(queries.shape[0]),
+                                   float(quantile), float(lr), loss.ctypes.data if want_loss else None,
+                                   _stream_ptr(stream)), "fps_mlp_train_step")
+    return float(loss[0]) if want_loss else None

@@ -18,6 +18,9 @@
 //                         smallest D with >= k accepted at distance <= D) and
 //                         tightens thr[q].  Popcount buckets whose lower bound
 //                         |popc q - b| exceeds thr[q] are skipped per query;
+//   (with predicted starting bounds instead of the pilot, a query whose bound was
+//   too low ends with fewer than k accepted records; the select kernel reports
+//   it as -2 and the host re-runs it exactly)
 //   batch_select_kernel   per query: hist is exact up to the final bound
 //                         (every record at distance <= the true k-th distance
 //                         was accepted and counted once), which gives the k-th
@@ -326,7 +329,13 @@ __global__ void __launch_bounds__(kSelThreads) batch_select_kernel(DevLib lib, B
     }
   }
   __syncthreads();
-  if (threadIdx.x == 0 && (s_nfin != cless || s_T >= kNumBuckets || s_ntie < need)) atomicOr(b.err, DEVERR_INTERNAL);
+  if (s_T >= kNumBuckets) {
+    // fewer than k records were accepted: the starting bound was below the true
+    // k-th distance (possible only with a predicted bound) -- exact fallback
+    if (threadIdx.x == 0) b.out_count[q] = -2;
+    return;
+  }
+  if (threadIdx.x == 0 && (s_nfin != cless || s_ntie < need)) atomicOr(b.err, DEVERR_INTERNAL);
   const int ntie = s_ntie;
   if (need > 0) {
     if (ntie <= kSelTies) {
@@ -385,6 +394,19 @@ constexpr int kQB = 64;
 cudaError_t batch_prepare(const DevLib& lib, const BatchDev& b, int use_pilot, cudaStream_t s) {
   if (b.Q == 0) return cudaSuccess;
   batch_prepare_kernel<<<b.Q, 256, 0, s>>>(lib, b, use_pilot);
+  return cudaGetLastError();
+}
+
+__global__ void thr_from_tau_kernel(BatchDev b, const float* tau) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= b.Q) return;
+  const float t = ceilf(tau[q]);
+  b.thr[q] = t <= 0.f ? 0u : (t >= 166.f ? 166u : static_cast<uint32_t>(t));
+}
+
+cudaError_t batch_thr_from_tau(const BatchDev& b, const float* tau, cudaStream_t s) {
+  if (b.Q == 0) return cudaSuccess;
+  thr_from_tau_kernel<<<(b.Q + 255) / 256, 256, 0, s>>>(b, tau);
   return cudaGetLastError();
 }
 

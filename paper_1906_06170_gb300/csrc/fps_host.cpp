@@ -538,7 +538,7 @@ int64_t batch_cap(int k, int64_t n) {
 fps_status batch_kernels(Library* L, Workspace* w, int path, const uint64_t* queries, int Q, const int32_t* k,
                          const int64_t* off, int64_t total, int32_t* out_index, int32_t* out_dist,
                          int32_t* out_count, const fps_search_opts* opts, bool dev_io, cudaStream_t s,
-                         int64_t* n_fallback) {
+                         int64_t* n_fallback, const float* learned_tau) {
   const bool tc = path == FPS_PATH_TC_FP8;
   std::vector<int64_t> coff(static_cast<size_t>(Q) + 1, 0);
   for (int q = 0; q < Q; ++q) coff[q + 1] = coff[q] + batch_cap(k[q], L->n);
@@ -547,14 +547,16 @@ fps_status batch_kernels(Library* L, Workspace* w, int path, const uint64_t* que
   const size_t d_k = dv.take(sizeof(int32_t) * Q);
   const size_t d_co = dv.take(sizeof(int64_t) * (Q + 1));
   const size_t d_oo = dv.take(sizeof(int64_t) * (Q + 1));
+  const bool learned = learned_tau != nullptr;
+  const size_t d_tau = dv.take(learned && !dev_io ? sizeof(float) * Q : 0);
   const size_t plan_end = dv.at;
   const size_t d_thr = dv.take(sizeof(uint32_t) * Q);
-  const size_t d_cnt = dv.take(sizeof(uint32_t) * Q);
   const size_t d_hist = dv.take(sizeof(uint32_t) * 168 * Q);
   const size_t d_work = dv.take(sizeof(uint32_t));
   const size_t d_oi = dv.take(dev_io ? 0 : sizeof(int32_t) * total);
   const size_t d_od = dv.take(dev_io ? 0 : sizeof(int32_t) * total);
   const size_t d_oc = dv.take(sizeof(int32_t) * Q);
+  const size_t d_cnt = dv.take(sizeof(uint32_t) * Q);   // copied back with the counts (statistics)
   const size_t d_cand = dv.take(sizeof(unsigned long long) * static_cast<size_t>(coff[Q]));
   const size_t out_begin = dev_io ? d_oc : d_oi, out_end = d_cand;
   const size_t d_qop = dv.take(tc ? tc_query_operand_bytes(Q) : 0);
@@ -566,6 +568,7 @@ fps_status batch_kernels(Library* L, Workspace* w, int path, const uint64_t* que
   std::memcpy(hb + d_k, k, sizeof(int32_t) * Q);
   std::memcpy(hb + d_co, coff.data(), sizeof(int64_t) * (Q + 1));
   std::memcpy(hb + d_oo, off, sizeof(int64_t) * (Q + 1));
+  if (learned && !dev_io) std::memcpy(hb + d_tau, learned_tau, sizeof(float) * Q);
   if (cudaMemcpyAsync(db, hb, plan_end, cudaMemcpyHostToDevice, s) != cudaSuccess) {
     cudaGetLastError();
     return FPS_ERR_CUDA;
@@ -584,7 +587,9 @@ fps_status batch_kernels(Library* L, Workspace* w, int path, const uint64_t* que
   b.out_dist = dev_io ? out_dist : reinterpret_cast<int32_t*>(db + d_od);
   b.out_count = reinterpret_cast<int32_t*>(db + d_oc);
   b.err = &w->io->err;
-  cudaError_t ce = batch_prepare(L->dev, b, 1, s);
+  cudaError_t ce = batch_prepare(L->dev, b, learned ? 0 : 1, s);
+  if (ce == cudaSuccess && learned)
+    ce = batch_thr_from_tau(b, dev_io ? learned_tau : reinterpret_cast<const float*>(db + d_tau), s);
   if (ce == cudaSuccess) {
     if (tc) {
       uint8_t* qop = reinterpret_cast<uint8_t*>(db + d_qop);
@@ -609,6 +614,10 @@ fps_status batch_kernels(Library* L, Workspace* w, int path, const uint64_t* que
   st = take_device_error(w, s);
   if (st != FPS_OK) return st;
   const int32_t* hc = reinterpret_cast<const int32_t*>(hb + d_oc);
+  const uint32_t* hcnt = reinterpret_cast<const uint32_t*>(hb + d_cnt);
+  int64_t accepted = 0;
+  for (int q = 0; q < Q; ++q) accepted += hcnt[q];
+  if (opts && opts->stats) opts->stats->candidates = accepted;
   const double tmo = opt_timeout(opts);
   int64_t nf = 0;
   for (int q = 0; q < Q; ++q) {
@@ -658,6 +667,12 @@ fps_status search_batch_impl(Library* L, const uint64_t* queries, int Q, const i
   if (st != FPS_OK) return st;
   const double tmo = opt_timeout(opts);
   int path = opts ? opts->path : FPS_PATH_AUTO;
+  const float* tau = nullptr;
+  if (path == FPS_PATH_LEARNED) {
+    if (!opts->tau) return FPS_ERR_INVALID_ARG;
+    tau = opts->tau;                      // predicted bounds replace the pilot; the scan itself is chosen below
+    path = FPS_PATH_AUTO;
+  }
   if (path == FPS_PATH_AUTO) path = (L->tc_fp8 && Q >= 64) ? FPS_PATH_TC_FP8 : FPS_PATH_POPC_BATCH;
   if (path == FPS_PATH_TC_FP8 && !L->tc_fp8) return FPS_ERR_UNSUPPORTED;
   if (path != FPS_PATH_POPC) {
@@ -666,12 +681,12 @@ fps_status search_batch_impl(Library* L, const uint64_t* queries, int Q, const i
       for (int q = 0; q < Q; ++q)
         if (queries[3 * q + 2] >> (kBits - 128)) return FPS_ERR_INVALID_ARG;
     int64_t nf = 0;
-    st = batch_kernels(L, w, path, queries, Q, k, off, total, out_index, out_dist, out_count, opts, dev_io, s, &nf);
+    st = batch_kernels(L, w, path, queries, Q, k, off, total, out_index, out_dist, out_count, opts, dev_io, s, &nf,
+                       tau);
     if (st == FPS_OK && opts && opts->stats) {
       opts->stats->queries = Q;
       opts->stats->fallbacks = nf;
-      opts->stats->candidates = 0;
-      opts->stats->path_used = path;
+      opts->stats->path_used = tau ? FPS_PATH_LEARNED : path;
     }
     return st;
   }

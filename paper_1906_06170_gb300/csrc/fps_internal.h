@@ -123,6 +123,8 @@ struct BatchDev {
 
 // ---- batched kernels (fps_batch.cu)
 cudaError_t batch_prepare(const DevLib& lib, const BatchDev& b, int use_pilot, cudaStream_t s);
+// Starting bounds from predicted distances: thr[q] = clamp(ceil(tau[q]), 0, 166).
+cudaError_t batch_thr_from_tau(const BatchDev& b, const float* tau, cudaStream_t s);
 cudaError_t batch_scan_popc(const DevLib& lib, const BatchDev& b, int num_sms, uint32_t* work_counter,
                             cudaStream_t s);
 cudaError_t batch_select(const DevLib& lib, const BatchDev& b, cudaStream_t s);

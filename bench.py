@@ -49,7 +49,7 @@ def parse_args():
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--n", type=int, default=PAPER_N, help="library records")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--workload", default="single", choices=["single", "batch"],
+    p.add_argument("--workload", default="single", choices=["single", "batch", "learned", "serve"],
                    help="single: 16 sequential single queries per step (default); "
                         "batch: --queries queries with mixed k in one batched call per step")
     p.add_argument("--queries", type=int, default=4096)
@@ -381,12 +381,168 @@ def run_batch(args):
     fps.fps_release(lib)
 
 
+def run_learned(args):
+    """Learned threshold: train on exact T_30 of 4 x 10M-record libraries, search the full library."""
+    import torch
+
+    import paper_1906_06170_gb300 as fps
+    import synth
+    from paper_1906_06170_gb300 import learn
+
+    torch.cuda.set_device(0)
+    k, Q = 30, args.queries
+    n_train_lib = int(os.environ.get("FPS_LEARN_TRAIN_N", 10_000_000))
+    per_lib = int(os.environ.get("FPS_LEARN_PER_LIB", 500_000))
+    t_prep = time.perf_counter()
+    qs_all, ts_all = [], []
+    for seed in (1, 2, 3, 4):
+        lib = fps.fps_library_load(packed=synth.packed(n_train_lib, seed), flags=fps.FPS_LOAD_TC_OPERAND)
+        q = torch.from_numpy(synth.packed(per_lib, 100 + seed).view(np.int64).copy()).cuda()
+        ts_all.append(learn.exact_kth(lib, q, k))
+        qs_all.append(q)
+        fps.fps_release(lib)
+    qtr, ttr = torch.cat(qs_all), torch.cat(ts_all)
+    t_labels = time.perf_counter() - t_prep
+    model = fps.fps_mlp_create(0)
+    fps.fps_mlp_set_params(model, learn.init_params(0))
+    t0 = time.perf_counter()
+    hist = learn.train(model, qtr, ttr, epochs=int(os.environ.get("FPS_LEARN_EPOCHS", 6)), batch=4096, lr=2e-3,
+                       quantile=0.9)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del qtr, ttr
+
+    n = args.n
+    lib = fps.fps_library_load(packed=synth.packed(n, 0), flags=fps.FPS_LOAD_TC_OPERAND)
+    qcal = torch.from_numpy(synth.packed(4096, 999).view(np.int64).copy()).cuda()
+    offset = learn.calibrate_offset(model, qcal, learn.exact_kth(lib, qcal, k), max_fallback=0.0025)
+    qs = synth.packed(Q, synth.query_seed(3))
+    qd = torch.from_numpy(qs.view(np.int64).copy()).cuda()
+    ks = np.full(Q, k, np.int32)
+    off = fps.batch_offsets(ks)
+    oi = torch.empty(int(off[-1]), dtype=torch.int32, device="cuda")
+    od = torch.empty_like(oi)
+    oc = torch.empty(Q, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / steps
+
+    st_l = fps.fps_search_stats()
+
+    def learned_step():
+        tau = learn.predict_tau(model, qd, offset).contiguous()
+        fps.fps_search_batch(lib, qd, ks, path=fps.FPS_PATH_LEARNED, tau=tau, out_index=oi, out_dist=od,
+                             out_count=oc, offsets=off, stream=stream, stats=st_l)
+
+    clocks = ClockSampler(0)
+    clocks.start()
+    ms_l = timed(learned_step, args.steps, args.warmup)
+    clk = clocks.stop()
+    res_l = (oi.clone(), od.clone())
+    st_p = fps.fps_search_stats()
+
+    def pilot_step():
+        fps.fps_search_batch(lib, qd, ks, path=fps.FPS_PATH_TC_FP8, out_index=oi, out_dist=od, out_count=oc,
+                             offsets=off, stream=stream, stats=st_p)
+
+    ms_p = timed(pilot_step, max(2, args.steps // 2), 1)
+    assert torch.equal(res_l[0], oi) and torch.equal(res_l[1], od), "learned and sampled-bound results differ"
+    value = Q * n / (ms_l / 1e3) / 1e9
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_l, "higher_is_better": True, "scaling": "weak",
+            "queries_per_s": Q / (ms_l / 1e3), "dtype": "fp8+bf16", "data": "synthetic",
+            "fallbacks": int(st_l.fallbacks), "fallback_rate": st_l.fallbacks / Q,
+            "candidates_learned": int(st_l.candidates), "candidates_sampled_bound": int(st_p.candidates),
+            "calibration_offset": offset, "train_loss_per_epoch": hist,
+            "sampled_bound_tc": {"ms_per_step": ms_p, "queries_per_s": Q / (ms_p / 1e3),
+                                 "value": Q * n / (ms_p / 1e3) / 1e9},
+            "setup_s": {"labels": round(t_labels, 1), "train": round(t_train, 1)},
+            "config": {"workload": f"learned threshold: MLP 167-256-256-1 trained on {4 * per_lib:,} (query, 30th "
+                                   f"distance) pairs from 4 x {n_train_lib:,}-record libraries (seeds 1-4); search "
+                                   f"{n:,} records (seed 0), {Q} queries (seed 1003), k={k}",
+                       "n_records": n, "queries": Q, "k": k},
+            "clocks": clk}
+    print(json.dumps(line), flush=True)
+    fps.fps_mlp_release(model)
+    fps.fps_release(lib)
+
+
+def run_serve(args):
+    """Serving loop: Poisson arrivals against three resident libraries, dynamic batches vs one at a time."""
+    import torch
+
+    import paper_1906_06170_gb300 as fps
+    import synth
+    from paper_1906_06170_gb300 import serve
+
+    torch.cuda.set_device(0)
+    sizes = {"1M": (1_000_000, 10), "20M": (20_000_000, 11), "95M": (args.n, 12)}
+    libs, need = {}, 0
+    for nm, (n, seed) in sizes.items():
+        libs[nm] = fps.fps_library_load(packed=synth.packed(n, seed), flags=fps.FPS_LOAD_TC_OPERAND)
+        need += fps.fps_library_info_get(libs[nm])["device_bytes"]
+    # admission: a budget that fits the two small libraries refuses the large one
+    small = need - fps.fps_library_info_get(libs["95M"])["device_bytes"]
+    try:
+        fps.fps_release(fps.fps_library_load(packed=synth.packed(1000, 12), hbm_budget_bytes=1))
+        refused = False
+    except fps.FpsError as e:
+        refused = e.status == fps.FPS_ERR_BUDGET
+    rate = float(os.environ.get("FPS_SERVE_RATE", 5000))
+    nreq = int(os.environ.get("FPS_SERVE_REQUESTS", 20000))
+    arr = serve.poisson_arrivals(nreq, rate, seed=5)
+    qs = synth.packed(nreq, 1004)
+    names = list(sizes)
+
+    def requests():
+        return [serve.Request(float(t), names[synth.draw(5, i, 1) % 3], qs[i], [10, 30, 100][synth.draw(5, i, 2) % 3])
+                for i, t in enumerate(arr)]
+
+    srv = serve.Server(libs, has_tc={nm: True for nm in names}, max_batch=512)
+    srv.run(requests()[:200], keep_results=False)                 # warm-up (workspaces, first launches)
+    srv.batch_sizes.clear()
+    clocks = ClockSampler(0)
+    clocks.start()
+    batched = serve.latency_stats(srv.run(requests(), keep_results=False))
+    clk = clocks.stop()
+    sizes_seen = np.array(srv.batch_sizes)
+    n_plain = min(nreq, int(os.environ.get("FPS_SERVE_PLAIN_REQUESTS", 4000)))
+    plain = serve.latency_stats(srv.run(requests()[:n_plain], batched=False, keep_results=False))
+    line = {"metric": "serving: requests/s and latency, exact top-k", "value": batched["throughput_rps"],
+            "unit": "requests/s", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
+            "batched": batched, "plain_per_query": plain,
+            "batch_size": {"mean": float(sizes_seen.mean()), "max": int(sizes_seen.max()), "calls": int(sizes_seen.size)},
+            "budget_refusal_ok": refused, "device_bytes_resident": need,
+            "config": {"workload": f"Poisson arrivals at {rate:g} req/s, {nreq} requests, k from {{10,30,100}}, "
+                                   f"libraries 1M/20M/{args.n:,} (seeds 10/11/12) chosen uniformly, dynamic batches "
+                                   "of 1-512 per library; plain = one fps_search_packed per request "
+                                   f"(first {n_plain} requests)"},
+            "clocks": clk}
+    print(json.dumps(line), flush=True)
+    for lib in libs.values():
+        fps.fps_release(lib)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch":
         run_batch(args)
+    elif args.workload == "learned":
+        run_learned(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_gb300(args)
 

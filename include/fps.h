@@ -244,6 +244,17 @@ fps_status fps_mlp_grad(fps_mlp mlp, const uint64_t* queries, const float* targe
 fps_status fps_mlp_train_step(fps_mlp mlp, const uint64_t* queries, const float* targets, int B, float quantile,
                               float lr, float* loss_host, void* cuda_stream);
 
+/*
+ * "Combined and sorted" (the text after Fig. 3: several library files are
+ * searched separately and their results merged): k-way merge of `parts`
+ * result lists, each already in ascending (distance, index) order with
+ * indices global to the combined library.  List p holds the entries
+ * [part_off[p], part_off[p+1]) of idx/dist (host arrays).  Writes the first
+ * min(k, total) entries of the combined order; *out_n their number.  Host only.
+ */
+fps_status fps_merge_topk(const int32_t* idx, const int32_t* dist, const int64_t* part_off, int parts, int k,
+                          int32_t* out_index, int32_t* out_dist, int* out_n);
+
 /* ----------------------------------------------------------------- helpers */
 
 const char* fps_status_string(fps_status st);

@@ -72,6 +72,7 @@ _lib.fps_search_packed.argtypes = [_vp, _vp, _i32, _vp, _vp, _vp, ctypes.POINTER
 _lib.fps_search_batch.argtypes = [_vp, _vp, _i32, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(fps_search_opts), _vp]
 _lib.fps_sync.argtypes = [_vp, _vp]
 _lib.fps_search_noalloc.argtypes = [_vp, _vp, _i32, _vp, _vp, _vp, _vp]
+_lib.fps_merge_topk.argtypes = [_vp, _vp, _vp, _i32, _i32, _vp, _vp, ctypes.POINTER(_i32)]
 _lib.fps_mlp_param_count.restype = ctypes.c_size_t
 _lib.fps_mlp_create.argtypes = [_i32, ctypes.POINTER(_vp)]
 _lib.fps_mlp_release.argtypes = [_vp]
@@ -86,7 +87,7 @@ _lib.fps_pack_text.argtypes = [_vp, ctypes.c_size_t, ctypes.c_uint32, _vp, _vp, 
 for _f in ("fps_library_load", "fps_release", "fps_library_info_get", "fps_library_cid", "fps_search",
            "fps_search_packed", "fps_search_batch", "fps_sync", "fps_pack_query", "fps_pack_text", "fps_search_noalloc",
            "fps_mlp_create", "fps_mlp_release", "fps_mlp_set_params", "fps_mlp_get_params", "fps_mlp_predict",
-           "fps_mlp_grad", "fps_mlp_train_step"):
+           "fps_mlp_grad", "fps_mlp_train_step", "fps_merge_topk"):
     getattr(_lib, _f).restype = _i32
 
 
@@ -311,6 +312,20 @@ def fps_search_noalloc(lib: Library, query, k: int, out_index, out_dist, out_cou
                                  out_count.data_ptr(), _stream_ptr(stream))
     _check(st, "fps_search_noalloc")
     return out_index, out_dist, out_count
+
+
+def fps_merge_topk(parts, k: int):
+    """Merge per-shard (index, distance) lists (each ascending, global indices) into the combined top-k."""
+    idx = np.ascontiguousarray(np.concatenate([np.asarray(a, np.int32) for a, _ in parts] or [np.zeros(0, np.int32)]))
+    dist = np.ascontiguousarray(np.concatenate([np.asarray(b, np.int32) for _, b in parts] or [np.zeros(0, np.int32)]))
+    off = np.zeros(len(parts) + 1, np.int64)
+    off[1:] = np.cumsum([len(a) for a, _ in parts])
+    oi, od = np.zeros(max(k, 1), np.int32), np.zeros(max(k, 1), np.int32)
+    n = _i32(0)
+    _check(_lib.fps_merge_topk(idx.ctypes.data if idx.size else None, dist.ctypes.data if dist.size else None,
+                               off.ctypes.data, len(parts), int(k), oi.ctypes.data, od.ctypes.data, ctypes.byref(n)),
+           "fps_merge_topk")
+    return oi[: n.value], od[: n.value]
 
 
 def fps_sync(lib: Library, stream=None):

@@ -932,6 +932,41 @@ fps_status fps_search_batch(fps_library lib, const uint64_t* queries, int Q, con
   return search_batch_impl(L, queries, Q, k, out_offsets, total, out_index, out_dist, out_count, opts, dev_io, s);
 }
 
+fps_status fps_merge_topk(const int32_t* idx, const int32_t* dist, const int64_t* part_off, int parts, int k,
+                          int32_t* out_index, int32_t* out_dist, int* out_n) {
+  if (parts < 0 || k < 0 || !part_off || !out_n || (k > 0 && (!out_index || !out_dist))) return FPS_ERR_INVALID_ARG;
+  for (int p = 0; p < parts; ++p)
+    if (part_off[p + 1] < part_off[p] || (part_off[p + 1] > part_off[p] && (!idx || !dist))) return FPS_ERR_INVALID_ARG;
+  // a heap of the current head of every list, ordered by (distance, index)
+  using Head = std::pair<uint64_t, int>;
+  auto key = [&](int64_t e) {
+    return (static_cast<uint64_t>(static_cast<uint32_t>(dist[e])) << 32) | static_cast<uint32_t>(idx[e]);
+  };
+  std::vector<Head> heap;
+  std::vector<int64_t> pos(parts);
+  for (int p = 0; p < parts; ++p) {
+    pos[p] = part_off[p];
+    if (pos[p] < part_off[p + 1]) heap.emplace_back(key(pos[p]), p);
+  }
+  auto cmp = [](const Head& a, const Head& b) { return a > b; };
+  std::make_heap(heap.begin(), heap.end(), cmp);
+  int n = 0;
+  while (n < k && !heap.empty()) {
+    std::pop_heap(heap.begin(), heap.end(), cmp);
+    const int p = heap.back().second;
+    heap.pop_back();
+    out_index[n] = idx[pos[p]];
+    out_dist[n] = dist[pos[p]];
+    ++n;
+    if (++pos[p] < part_off[p + 1]) {
+      heap.emplace_back(key(pos[p]), p);
+      std::push_heap(heap.begin(), heap.end(), cmp);
+    }
+  }
+  *out_n = n;
+  return FPS_OK;
+}
+
 fps_status fps_sync(fps_library lib, void* cuda_stream) {
   if (!lib) return FPS_ERR_INVALID_ARG;
   Library* L = reinterpret_cast<Library*>(lib);

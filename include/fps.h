@@ -122,7 +122,8 @@ fps_status fps_library_cid(fps_library lib, int64_t index, int64_t* cid);
 /* --------------------------------------------------------------- searching */
 
 typedef enum {
-  FPS_PATH_AUTO = 0,     /* let the library choose (autotuned) */
+  FPS_PATH_AUTO = 0,     /* batch calls: the first batch of each size class (ceil log2 Q) times the popcount
+                            and tensor-core batch paths and keeps the faster for this library */
   FPS_PATH_POPC = 1,     /* popcount scan: one launch per query (single-query kernel) */
   FPS_PATH_POPC_BATCH = 2, /* popcount scan, many queries per launch */
   FPS_PATH_TC_FP8 = 3,   /* tensor-core contraction on 0/1 FP8 operands */
@@ -207,6 +208,23 @@ fps_status fps_search_batch(fps_library lib, const uint64_t* queries, int Q, con
 #define FPS_NOALLOC_K_MAX 128
 fps_status fps_search_noalloc(fps_library lib, const uint64_t* query, int k, int32_t* out_index, int32_t* out_dist,
                               int32_t* out_count, void* cuda_stream);
+
+/*
+ * A batch whose shape is fixed -- Q queries with per-query k[q] (host array),
+ * path FPS_PATH_POPC_BATCH, FPS_PATH_TC_FP8 or FPS_PATH_AUTO, optionally
+ * learned bounds -- captured once as a CUDA graph with its own buffers: copy
+ * of the plan in, bounds, scan, per-query select, results out.  Each run takes
+ * host queries (Q x FPS_WORDS) and, when learned, host predictions tau[Q];
+ * results go to host arrays laid out by the prefix sums of k (as in
+ * fps_search_batch); the call returns when they are written.  Queries that
+ * need the exact fallback are re-run after the graph.  A plan must not be run
+ * concurrently with itself; it must be released before its library.
+ */
+typedef struct fps_batch_plan_s* fps_batch_plan;
+fps_status fps_batch_plan_create(fps_library lib, int Q, const int32_t* k, int path, int learned, fps_batch_plan* out);
+fps_status fps_batch_plan_run(fps_batch_plan plan, const uint64_t* queries, const float* tau, int32_t* out_index,
+                              int32_t* out_dist, int32_t* out_count, fps_search_stats* stats, void* cuda_stream);
+fps_status fps_batch_plan_release(fps_batch_plan plan);
 
 /* Wait for cuda_stream and report (then clear) any device-side error of searches enqueued on it. */
 fps_status fps_sync(fps_library lib, void* cuda_stream);

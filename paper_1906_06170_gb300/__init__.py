@@ -73,6 +73,9 @@ _lib.fps_search_batch.argtypes = [_vp, _vp, _i32, _vp, _vp, _vp, _vp, _vp, ctype
 _lib.fps_sync.argtypes = [_vp, _vp]
 _lib.fps_search_noalloc.argtypes = [_vp, _vp, _i32, _vp, _vp, _vp, _vp]
 _lib.fps_merge_topk.argtypes = [_vp, _vp, _vp, _i32, _i32, _vp, _vp, ctypes.POINTER(_i32)]
+_lib.fps_batch_plan_create.argtypes = [_vp, _i32, _vp, _i32, _i32, ctypes.POINTER(_vp)]
+_lib.fps_batch_plan_run.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(fps_search_stats), _vp]
+_lib.fps_batch_plan_release.argtypes = [_vp]
 _lib.fps_mlp_param_count.restype = ctypes.c_size_t
 _lib.fps_mlp_create.argtypes = [_i32, ctypes.POINTER(_vp)]
 _lib.fps_mlp_release.argtypes = [_vp]
@@ -87,7 +90,8 @@ _lib.fps_pack_text.argtypes = [_vp, ctypes.c_size_t, ctypes.c_uint32, _vp, _vp, 
 for _f in ("fps_library_load", "fps_release", "fps_library_info_get", "fps_library_cid", "fps_search",
            "fps_search_packed", "fps_search_batch", "fps_sync", "fps_pack_query", "fps_pack_text", "fps_search_noalloc",
            "fps_mlp_create", "fps_mlp_release", "fps_mlp_set_params", "fps_mlp_get_params", "fps_mlp_predict",
-           "fps_mlp_grad", "fps_mlp_train_step", "fps_merge_topk"):
+           "fps_mlp_grad", "fps_mlp_train_step", "fps_merge_topk", "fps_batch_plan_create", "fps_batch_plan_run",
+           "fps_batch_plan_release"):
     getattr(_lib, _f).restype = _i32
 
 
@@ -424,3 +428,40 @@ def fps_mlp_train_step(m: Mlp, queries, targets, quantile: float, lr: float, wan
                                    float(quantile), float(lr), loss.ctypes.data if want_loss else None,
                                    _stream_ptr(stream)), "fps_mlp_train_step")
     return float(loss[0]) if want_loss else None
+
+
+# ------------------------------------------------------------ graph-captured batch plan
+class BatchPlan:
+    def __init__(self, handle, k):
+        self.handle = handle
+        self.k = np.ascontiguousarray(np.asarray(k, np.int32))
+        self.off = batch_offsets(self.k)
+
+
+def fps_batch_plan_create(lib: Library, k, path: int = FPS_PATH_AUTO, learned: bool = False) -> BatchPlan:
+    kk = np.ascontiguousarray(np.asarray(k, np.int32).reshape(-1))
+    h = _vp()
+    _check(_lib.fps_batch_plan_create(lib._h, kk.size, kk.ctypes.data, int(path), int(learned), ctypes.byref(h)),
+           "fps_batch_plan_create")
+    return BatchPlan(h.value, kk)
+
+
+def fps_batch_plan_run(plan: BatchPlan, queries, tau=None, stats=None, stream=None):
+    """Run a captured batch on host queries [Q, 3]; returns a list of (index, distance) per query."""
+    q = np.ascontiguousarray(np.asarray(queries, dtype=np.uint64).reshape(-1, FPS_WORDS))
+    Q = plan.k.size
+    total = max(int(plan.off[-1]), 1)
+    idx, dist, cnt = np.zeros(total, np.int32), np.zeros(total, np.int32), np.zeros(Q, np.int32)
+    t = np.ascontiguousarray(np.asarray(tau, np.float32)) if tau is not None else None
+    st_obj = stats if stats is not None else fps_search_stats()
+    _check(_lib.fps_batch_plan_run(plan.handle, q.ctypes.data, t.ctypes.data if t is not None else None,
+                                   idx.ctypes.data, dist.ctypes.data, cnt.ctypes.data, ctypes.byref(st_obj),
+                                   _stream_ptr(stream)), "fps_batch_plan_run")
+    off = plan.off
+    return [(idx[off[i]: off[i] + cnt[i]].copy(), dist[off[i]: off[i] + cnt[i]].copy()) for i in range(Q)]
+
+
+def fps_batch_plan_release(plan: BatchPlan):
+    if plan is not None and plan.handle:
+        _check(_lib.fps_batch_plan_release(plan.handle), "fps_batch_plan_release")
+        plan.handle = None

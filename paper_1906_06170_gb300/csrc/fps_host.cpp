@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <atomic>
 #include <cstdio>
 #include <cstdlib>
@@ -535,91 +536,105 @@ int64_t batch_cap(int k, int64_t n) {
 }
 
 // Many queries per launch with the batched kernels (pilot bound, scan, per-query select).
-fps_status batch_kernels(Library* L, Workspace* w, int path, const uint64_t* queries, int Q, const int32_t* k,
-                         const int64_t* off, int64_t total, int32_t* out_index, int32_t* out_dist,
-                         int32_t* out_count, const fps_search_opts* opts, bool dev_io, cudaStream_t s,
-                         int64_t* n_fallback, const float* learned_tau) {
-  const bool tc = path == FPS_PATH_TC_FP8;
-  std::vector<int64_t> coff(static_cast<size_t>(Q) + 1, 0);
-  for (int q = 0; q < Q; ++q) coff[q + 1] = coff[q] + batch_cap(k[q], L->n);
+// Byte layout of one batch's staging block (device), mirrored for the parts that
+// travel (the plan region goes host -> device, the output region back).
+struct BatchLayout {
+  size_t d_q, d_k, d_co, d_oo, d_tau, plan_end;
+  size_t d_thr, d_hist, d_work, d_oi, d_od, d_oc, d_cnt, d_cand, out_begin, out_end, d_qop, bytes;
+};
+
+BatchLayout batch_layout(int Q, int64_t total, int64_t cand_keys, bool dev_io, bool learned, bool tc) {
+  BatchLayout l{};
   Carve dv;
-  const size_t d_q = dv.take(dev_io ? 0 : sizeof(uint64_t) * 3 * Q);
-  const size_t d_k = dv.take(sizeof(int32_t) * Q);
-  const size_t d_co = dv.take(sizeof(int64_t) * (Q + 1));
-  const size_t d_oo = dv.take(sizeof(int64_t) * (Q + 1));
-  const bool learned = learned_tau != nullptr;
-  const size_t d_tau = dv.take(learned && !dev_io ? sizeof(float) * Q : 0);
-  const size_t plan_end = dv.at;
-  const size_t d_thr = dv.take(sizeof(uint32_t) * Q);
-  const size_t d_hist = dv.take(sizeof(uint32_t) * 168 * Q);
-  const size_t d_work = dv.take(sizeof(uint32_t));
-  const size_t d_oi = dv.take(dev_io ? 0 : sizeof(int32_t) * total);
-  const size_t d_od = dv.take(dev_io ? 0 : sizeof(int32_t) * total);
-  const size_t d_oc = dv.take(sizeof(int32_t) * Q);
-  const size_t d_cnt = dv.take(sizeof(uint32_t) * Q);   // copied back with the counts (statistics)
-  const size_t d_cand = dv.take(sizeof(unsigned long long) * static_cast<size_t>(coff[Q]));
-  const size_t out_begin = dev_io ? d_oc : d_oi, out_end = d_cand;
-  const size_t d_qop = dv.take(tc ? tc_query_operand_bytes(Q) : 0);
-  fps_status st = batch_staging(w, dv.at, plan_end > out_end ? plan_end : out_end);
-  if (st != FPS_OK) return st;
-  char* db = static_cast<char*>(w->batch_block);
-  char* hb = static_cast<char*>(w->batch_host);
-  if (!dev_io) std::memcpy(hb + d_q, queries, sizeof(uint64_t) * 3 * Q);
-  std::memcpy(hb + d_k, k, sizeof(int32_t) * Q);
-  std::memcpy(hb + d_co, coff.data(), sizeof(int64_t) * (Q + 1));
-  std::memcpy(hb + d_oo, off, sizeof(int64_t) * (Q + 1));
-  if (learned && !dev_io) std::memcpy(hb + d_tau, learned_tau, sizeof(float) * Q);
-  if (cudaMemcpyAsync(db, hb, plan_end, cudaMemcpyHostToDevice, s) != cudaSuccess) {
-    cudaGetLastError();
-    return FPS_ERR_CUDA;
-  }
+  l.d_q = dv.take(dev_io ? 0 : sizeof(uint64_t) * 3 * Q);
+  l.d_k = dv.take(sizeof(int32_t) * Q);
+  l.d_co = dv.take(sizeof(int64_t) * (Q + 1));
+  l.d_oo = dv.take(sizeof(int64_t) * (Q + 1));
+  l.d_tau = dv.take(learned && !dev_io ? sizeof(float) * Q : 0);
+  l.plan_end = dv.at;
+  l.d_thr = dv.take(sizeof(uint32_t) * Q);
+  l.d_hist = dv.take(sizeof(uint32_t) * 168 * Q);
+  l.d_work = dv.take(sizeof(uint32_t));
+  l.d_oi = dv.take(dev_io ? 0 : sizeof(int32_t) * total);
+  l.d_od = dv.take(dev_io ? 0 : sizeof(int32_t) * total);
+  l.d_oc = dv.take(sizeof(int32_t) * Q);
+  l.d_cnt = dv.take(sizeof(uint32_t) * Q);   // copied back with the counts (statistics)
+  l.d_cand = dv.take(sizeof(unsigned long long) * static_cast<size_t>(cand_keys));
+  l.out_begin = dev_io ? l.d_oc : l.d_oi;
+  l.out_end = l.d_cand;
+  l.d_qop = dv.take(tc ? tc_query_operand_bytes(Q) : 0);
+  l.bytes = dv.at;
+  return l;
+}
+
+std::vector<int64_t> batch_cand_offsets(const int32_t* k, int Q, int64_t n) {
+  std::vector<int64_t> coff(static_cast<size_t>(Q) + 1, 0);
+  for (int q = 0; q < Q; ++q) coff[q + 1] = coff[q] + batch_cap(k[q], n);
+  return coff;
+}
+
+// Host side of the plan region: queries (host form), k, candidate and output offsets, predicted bounds.
+void fill_plan(char* hb, const BatchLayout& l, const uint64_t* queries, int Q, const int32_t* k,
+               const std::vector<int64_t>& coff, const int64_t* off, const float* tau, bool dev_io) {
+  if (!dev_io) std::memcpy(hb + l.d_q, queries, sizeof(uint64_t) * 3 * Q);
+  std::memcpy(hb + l.d_k, k, sizeof(int32_t) * Q);
+  std::memcpy(hb + l.d_co, coff.data(), sizeof(int64_t) * (Q + 1));
+  std::memcpy(hb + l.d_oo, off, sizeof(int64_t) * (Q + 1));
+  if (tau && !dev_io) std::memcpy(hb + l.d_tau, tau, sizeof(float) * Q);
+}
+
+BatchDev batch_dev(char* db, const BatchLayout& l, int Q, const uint64_t* dev_queries, int32_t* dev_oi,
+                   int32_t* dev_od, uint32_t* err) {
   BatchDev b{};
   b.Q = Q;
-  b.queries = dev_io ? queries : reinterpret_cast<const uint64_t*>(db + d_q);
-  b.k = reinterpret_cast<const int32_t*>(db + d_k);
-  b.cand_off = reinterpret_cast<const int64_t*>(db + d_co);
-  b.out_off = reinterpret_cast<const int64_t*>(db + d_oo);
-  b.thr = reinterpret_cast<uint32_t*>(db + d_thr);
-  b.cnt = reinterpret_cast<uint32_t*>(db + d_cnt);
-  b.hist = reinterpret_cast<uint32_t*>(db + d_hist);
-  b.cand = reinterpret_cast<unsigned long long*>(db + d_cand);
-  b.out_idx = dev_io ? out_index : reinterpret_cast<int32_t*>(db + d_oi);
-  b.out_dist = dev_io ? out_dist : reinterpret_cast<int32_t*>(db + d_od);
-  b.out_count = reinterpret_cast<int32_t*>(db + d_oc);
-  b.err = &w->io->err;
-  cudaError_t ce = batch_prepare(L->dev, b, learned ? 0 : 1, s);
-  if (ce == cudaSuccess && learned)
-    ce = batch_thr_from_tau(b, dev_io ? learned_tau : reinterpret_cast<const float*>(db + d_tau), s);
+  b.queries = dev_queries ? dev_queries : reinterpret_cast<const uint64_t*>(db + l.d_q);
+  b.k = reinterpret_cast<const int32_t*>(db + l.d_k);
+  b.cand_off = reinterpret_cast<const int64_t*>(db + l.d_co);
+  b.out_off = reinterpret_cast<const int64_t*>(db + l.d_oo);
+  b.thr = reinterpret_cast<uint32_t*>(db + l.d_thr);
+  b.cnt = reinterpret_cast<uint32_t*>(db + l.d_cnt);
+  b.hist = reinterpret_cast<uint32_t*>(db + l.d_hist);
+  b.cand = reinterpret_cast<unsigned long long*>(db + l.d_cand);
+  b.out_idx = dev_oi ? dev_oi : reinterpret_cast<int32_t*>(db + l.d_oi);
+  b.out_dist = dev_od ? dev_od : reinterpret_cast<int32_t*>(db + l.d_od);
+  b.out_count = reinterpret_cast<int32_t*>(db + l.d_oc);
+  b.err = err;
+  return b;
+}
+
+// The device work of one batch: bounds (sampled or predicted), scan, per-query select.
+cudaError_t enqueue_batch(Library* L, const BatchDev& b, char* db, const BatchLayout& l, bool tc,
+                          const float* tau_dev, double tmo, cudaStream_t s) {
+  cudaError_t ce = batch_prepare(L->dev, b, tau_dev ? 0 : 1, s);
+  if (ce == cudaSuccess && tau_dev) ce = batch_thr_from_tau(b, tau_dev, s);
   if (ce == cudaSuccess) {
     if (tc) {
-      uint8_t* qop = reinterpret_cast<uint8_t*>(db + d_qop);
-      ce = tc_pack_queries(b.queries, Q, qop, s);
-      if (ce == cudaSuccess) ce = tc_scan(L->dev, b, L->tc_fp8, qop, L->num_sms, opt_timeout(opts), s);
+      uint8_t* qop = reinterpret_cast<uint8_t*>(db + l.d_qop);
+      ce = tc_pack_queries(b.queries, b.Q, qop, s);
+      if (ce == cudaSuccess) ce = tc_scan(L->dev, b, L->tc_fp8, qop, L->num_sms, tmo, s);
     } else {
-      ce = batch_scan_popc(L->dev, b, L->num_sms, reinterpret_cast<uint32_t*>(db + d_work), s);
+      ce = batch_scan_popc(L->dev, b, L->num_sms, reinterpret_cast<uint32_t*>(db + l.d_work), s);
     }
   }
   if (ce == cudaSuccess) ce = batch_select(L->dev, b, s);
-  if (ce != cudaSuccess) {
-    cudaGetLastError();
-    return FPS_ERR_CUDA;
-  }
-  // results (host form) or just the counts (device form) come back once; queries whose
-  // candidates overflowed (count -2) are re-run exactly with the single-query scan
-  if (cudaMemcpyAsync(hb + out_begin, db + out_begin, out_end - out_begin, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-      cudaStreamSynchronize(s) != cudaSuccess) {
-    cudaGetLastError();
-    return FPS_ERR_CUDA;
-  }
-  st = take_device_error(w, s);
-  if (st != FPS_OK) return st;
-  const int32_t* hc = reinterpret_cast<const int32_t*>(hb + d_oc);
-  const uint32_t* hcnt = reinterpret_cast<const uint32_t*>(hb + d_cnt);
+  return ce;
+}
+
+// After the output region is back on the host: statistics, exact re-runs of
+// queries reported -2 (candidate overflow or a predicted bound too low), and
+// the copy of host-form results into the caller's arrays.
+fps_status finish_batch(Library* L, Workspace* w, const char* hb, const char* db, const BatchLayout& l,
+                        const uint64_t* queries, int Q, const int32_t* k, const int64_t* off, int32_t* out_index,
+                        int32_t* out_dist, int32_t* out_count, const fps_search_opts* opts, bool dev_io,
+                        cudaStream_t s, int64_t* n_fallback) {
+  const int32_t* hc = reinterpret_cast<const int32_t*>(hb + l.d_oc);
+  const uint32_t* hcnt = reinterpret_cast<const uint32_t*>(hb + l.d_cnt);
   int64_t accepted = 0;
   for (int q = 0; q < Q; ++q) accepted += hcnt[q];
   if (opts && opts->stats) opts->stats->candidates = accepted;
   const double tmo = opt_timeout(opts);
   int64_t nf = 0;
+  fps_status st = FPS_OK;
   for (int q = 0; q < Q; ++q) {
     if (hc[q] != -2) continue;
     ++nf;
@@ -631,7 +646,7 @@ fps_status batch_kernels(Library* L, Workspace* w, int path, const uint64_t* que
     }
   }
   if (dev_io) {
-    if (cudaMemcpyAsync(out_count, db + d_oc, sizeof(int32_t) * Q, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+    if (cudaMemcpyAsync(out_count, db + l.d_oc, sizeof(int32_t) * Q, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
       cudaGetLastError();
       return FPS_ERR_CUDA;
     }
@@ -645,8 +660,8 @@ fps_status batch_kernels(Library* L, Workspace* w, int path, const uint64_t* que
       }
     }
   } else {
-    const int32_t* hi = reinterpret_cast<const int32_t*>(hb + d_oi);
-    const int32_t* hd = reinterpret_cast<const int32_t*>(hb + d_od);
+    const int32_t* hi = reinterpret_cast<const int32_t*>(hb + l.d_oi);
+    const int32_t* hd = reinterpret_cast<const int32_t*>(hb + l.d_od);
     for (int q = 0; q < Q; ++q) {
       if (hc[q] == -2) continue;
       out_count[q] = hc[q];
@@ -656,6 +671,44 @@ fps_status batch_kernels(Library* L, Workspace* w, int path, const uint64_t* que
   }
   *n_fallback = nf;
   return FPS_OK;
+}
+
+// Many queries per launch with the batched kernels (bounds, scan, per-query select).
+fps_status batch_kernels(Library* L, Workspace* w, int path, const uint64_t* queries, int Q, const int32_t* k,
+                         const int64_t* off, int64_t total, int32_t* out_index, int32_t* out_dist,
+                         int32_t* out_count, const fps_search_opts* opts, bool dev_io, cudaStream_t s,
+                         int64_t* n_fallback, const float* learned_tau) {
+  const bool tc = path == FPS_PATH_TC_FP8;
+  const bool learned = learned_tau != nullptr;
+  std::vector<int64_t> coff = batch_cand_offsets(k, Q, L->n);
+  const BatchLayout l = batch_layout(Q, total, coff[Q], dev_io, learned, tc);
+  fps_status st = batch_staging(w, l.bytes, l.plan_end > l.out_end ? l.plan_end : l.out_end);
+  if (st != FPS_OK) return st;
+  char* db = static_cast<char*>(w->batch_block);
+  char* hb = static_cast<char*>(w->batch_host);
+  fill_plan(hb, l, queries, Q, k, coff, off, learned_tau, dev_io);
+  if (cudaMemcpyAsync(db, hb, l.plan_end, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+    cudaGetLastError();
+    return FPS_ERR_CUDA;
+  }
+  const BatchDev b = batch_dev(db, l, Q, dev_io ? queries : nullptr, dev_io ? out_index : nullptr,
+                               dev_io ? out_dist : nullptr, &w->io->err);
+  const float* tau_dev = learned ? (dev_io ? learned_tau : reinterpret_cast<const float*>(db + l.d_tau)) : nullptr;
+  if (enqueue_batch(L, b, db, l, tc, tau_dev, opt_timeout(opts), s) != cudaSuccess) {
+    cudaGetLastError();
+    return FPS_ERR_CUDA;
+  }
+  // results (host form) or just the counts (device form) come back once
+  if (cudaMemcpyAsync(hb + l.out_begin, db + l.out_begin, l.out_end - l.out_begin, cudaMemcpyDeviceToHost, s) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaGetLastError();
+    return FPS_ERR_CUDA;
+  }
+  st = take_device_error(w, s);
+  if (st != FPS_OK) return st;
+  return finish_batch(L, w, hb, db, l, queries, Q, k, off, out_index, out_dist, out_count, opts, dev_io, s,
+                      n_fallback);
 }
 
 fps_status search_batch_impl(Library* L, const uint64_t* queries, int Q, const int32_t* k, const int64_t* off,
@@ -673,7 +726,47 @@ fps_status search_batch_impl(Library* L, const uint64_t* queries, int Q, const i
     tau = opts->tau;                      // predicted bounds replace the pilot; the scan itself is chosen below
     path = FPS_PATH_AUTO;
   }
-  if (path == FPS_PATH_AUTO) path = (L->tc_fp8 && Q >= 64) ? FPS_PATH_TC_FP8 : FPS_PATH_POPC_BATCH;
+  if (path == FPS_PATH_AUTO && !L->tc_fp8) path = FPS_PATH_POPC_BATCH;
+  if (path == FPS_PATH_AUTO) {
+    // autotuner: the first batch of a size class runs both batched paths (identical, exact
+    // results) and the faster one is kept for that class of this library
+    int cls = 0;
+    while ((1 << cls) < Q) ++cls;
+    cls = cls * 2 + (tau ? 1 : 0);
+    int chosen = -1;
+    {
+      std::lock_guard<std::mutex> lock(L->mu);
+      auto it = L->tuned.find(cls);
+      if (it != L->tuned.end()) chosen = it->second;
+    }
+    if (chosen < 0) {
+      if (!dev_io)
+        for (int q = 0; q < Q; ++q)
+          if (queries[3 * q + 2] >> (kBits - 128)) return FPS_ERR_INVALID_ARG;
+      int64_t nf = 0;
+      auto t0 = std::chrono::steady_clock::now();
+      st = batch_kernels(L, w, FPS_PATH_POPC_BATCH, queries, Q, k, off, total, out_index, out_dist, out_count, opts,
+                         dev_io, s, &nf, tau);
+      if (st != FPS_OK) return st;
+      auto t1 = std::chrono::steady_clock::now();
+      st = batch_kernels(L, w, FPS_PATH_TC_FP8, queries, Q, k, off, total, out_index, out_dist, out_count, opts,
+                         dev_io, s, &nf, tau);
+      if (st != FPS_OK) return st;
+      auto t2 = std::chrono::steady_clock::now();
+      chosen = (t2 - t1) < (t1 - t0) ? FPS_PATH_TC_FP8 : FPS_PATH_POPC_BATCH;
+      {
+        std::lock_guard<std::mutex> lock(L->mu);
+        L->tuned[cls] = chosen;
+      }
+      if (opts && opts->stats) {
+        opts->stats->queries = Q;
+        opts->stats->fallbacks = nf;
+        opts->stats->path_used = tau ? FPS_PATH_LEARNED : FPS_PATH_TC_FP8;
+      }
+      return FPS_OK;
+    }
+    path = chosen;
+  }
   if (path == FPS_PATH_TC_FP8 && !L->tc_fp8) return FPS_ERR_UNSUPPORTED;
   if (path != FPS_PATH_POPC) {
     if (path != FPS_PATH_POPC_BATCH && path != FPS_PATH_TC_FP8) return FPS_ERR_UNSUPPORTED;  // TC_I8: no kind::i8
@@ -734,6 +827,51 @@ fps_status search_batch_impl(Library* L, const uint64_t* queries, int Q, const i
     opts->stats->path_used = FPS_PATH_POPC;
   }
   return FPS_OK;
+}
+
+// A batch whose shape (Q, k, path) is fixed: own buffers and one captured CUDA
+// graph (plan copy in, bounds, scan, select, results and error word out).
+struct BatchPlan {
+  Library* L = nullptr;
+  int Q = 0;
+  bool tc = false, learned = false;
+  std::vector<int32_t> k;
+  std::vector<int64_t> off, coff;
+  int64_t total = 0;
+  BatchLayout lay{};
+  char* db = nullptr;        // device block
+  char* hb = nullptr;        // pinned host mirror of the plan and output regions
+  uint32_t* err = nullptr;   // device error word
+  uint32_t* err_host = nullptr;
+  cudaStream_t cap = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+void free_plan(BatchPlan* P) {
+  if (!P) return;
+  DeviceGuard g(P->L ? P->L->device : 0);
+  if (P->exec) cudaGraphExecDestroy(P->exec);
+  if (P->graph) cudaGraphDestroy(P->graph);
+  if (P->cap) cudaStreamDestroy(P->cap);
+  if (P->db) cudaFree(P->db);
+  if (P->hb) cudaFreeHost(P->hb);
+  if (P->err) cudaFree(P->err);
+  if (P->err_host) cudaFreeHost(P->err_host);
+  delete P;
+}
+
+// Enqueue the whole batch on stream s (used once eagerly, then under capture).
+cudaError_t plan_enqueue(BatchPlan* P, double tmo, cudaStream_t s) {
+  const BatchDev b = batch_dev(P->db, P->lay, P->Q, nullptr, nullptr, nullptr, P->err);
+  const float* tau_dev = P->learned ? reinterpret_cast<const float*>(P->db + P->lay.d_tau) : nullptr;
+  cudaError_t e = cudaMemcpyAsync(P->db, P->hb, P->lay.plan_end, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = enqueue_batch(P->L, b, P->db, P->lay, P->tc, tau_dev, tmo, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(P->hb + P->lay.out_begin, P->db + P->lay.out_begin, P->lay.out_end - P->lay.out_begin,
+                        cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(P->err_host, P->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+  return e;
 }
 
 }  // namespace
@@ -964,6 +1102,107 @@ fps_status fps_merge_topk(const int32_t* idx, const int32_t* dist, const int64_t
     }
   }
   *out_n = n;
+  return FPS_OK;
+}
+
+fps_status fps_batch_plan_create(fps_library lib, int Q, const int32_t* k, int path, int learned,
+                                 fps_batch_plan* out) {
+  if (!lib || !out || Q <= 0 || !k) return FPS_ERR_INVALID_ARG;
+  *out = nullptr;
+  Library* L = reinterpret_cast<Library*>(lib);
+  if (path == FPS_PATH_AUTO) path = L->tc_fp8 ? FPS_PATH_TC_FP8 : FPS_PATH_POPC_BATCH;
+  if (path != FPS_PATH_POPC_BATCH && path != FPS_PATH_TC_FP8) return FPS_ERR_UNSUPPORTED;
+  if (path == FPS_PATH_TC_FP8 && !L->tc_fp8) return FPS_ERR_UNSUPPORTED;
+  BatchPlan* P = new (std::nothrow) BatchPlan();
+  if (!P) return FPS_ERR_NOMEM;
+  P->L = L;
+  P->Q = Q;
+  P->tc = path == FPS_PATH_TC_FP8;
+  P->learned = learned != 0;
+  P->k.assign(k, k + Q);
+  P->off.assign(static_cast<size_t>(Q) + 1, 0);
+  for (int q = 0; q < Q; ++q) {
+    fps_status st = check_k(k[q]);
+    if (st != FPS_OK) {
+      free_plan(P);
+      return st;
+    }
+    P->off[q + 1] = P->off[q] + k[q];
+  }
+  P->total = P->off[Q];
+  P->coff = batch_cand_offsets(k, Q, L->n);
+  P->lay = batch_layout(Q, P->total, P->coff[Q], false, P->learned, P->tc);
+  DeviceGuard g(L->device);
+  const size_t hbytes = P->lay.plan_end > P->lay.out_end ? P->lay.plan_end : P->lay.out_end;
+  if (!g.ok || cudaMalloc(&P->db, P->lay.bytes) != cudaSuccess || cudaMallocHost(&P->hb, hbytes) != cudaSuccess ||
+      cudaMalloc(&P->err, 256) != cudaSuccess || cudaMallocHost(&P->err_host, sizeof(uint32_t)) != cudaSuccess ||
+      cudaMemset(P->err, 0, 256) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&P->cap, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    free_plan(P);
+    return FPS_ERR_CUDA;
+  }
+  std::memset(P->hb, 0, hbytes);
+  fill_plan(P->hb, P->lay, nullptr, Q, P->k.data(), P->coff, P->off.data(), nullptr, true);
+  // one eager run (sets kernel attributes, checks the sequence), then capture the same sequence
+  cudaError_t e = plan_enqueue(P, 2.0, P->cap);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(P->cap);
+  if (e == cudaSuccess) e = cudaMemset(P->err, 0, 256);
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(P->cap, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaError_t e2 = plan_enqueue(P, 2.0, P->cap);
+    e = cudaStreamEndCapture(P->cap, &P->graph);
+    if (e2 != cudaSuccess) e = e2;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&P->exec, P->graph, 0);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    free_plan(P);
+    return FPS_ERR_CUDA;
+  }
+  *out = reinterpret_cast<fps_batch_plan>(P);
+  return FPS_OK;
+}
+
+fps_status fps_batch_plan_run(fps_batch_plan plan, const uint64_t* queries, const float* tau, int32_t* out_index,
+                              int32_t* out_dist, int32_t* out_count, fps_search_stats* stats, void* cuda_stream) {
+  if (!plan || !queries || !out_index || !out_dist || !out_count) return FPS_ERR_INVALID_ARG;
+  BatchPlan* P = reinterpret_cast<BatchPlan*>(plan);
+  if (P->learned && !tau) return FPS_ERR_INVALID_ARG;
+  for (int q = 0; q < P->Q; ++q)
+    if (queries[3 * q + 2] >> (kBits - 128)) return FPS_ERR_INVALID_ARG;
+  Library* L = P->L;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  DeviceGuard g(L->device);
+  if (!g.ok) return FPS_ERR_CUDA;
+  std::memcpy(P->hb + P->lay.d_q, queries, sizeof(uint64_t) * 3 * P->Q);
+  if (P->learned) std::memcpy(P->hb + P->lay.d_tau, tau, sizeof(float) * P->Q);
+  if (cudaGraphLaunch(P->exec, s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaGetLastError();
+    return FPS_ERR_CUDA;
+  }
+  if (*P->err_host) {
+    cudaMemset(P->err, 0, 256);
+    return (*P->err_host & DEVERR_TIMEOUT) ? FPS_ERR_TIMEOUT : FPS_ERR_OVERFLOW_INTERNAL;
+  }
+  Workspace* w = nullptr;
+  fps_status st = get_workspace(L, s, &w);
+  if (st != FPS_OK) return st;
+  fps_search_opts o{};
+  o.stats = stats;
+  int64_t nf = 0;
+  st = finish_batch(L, w, P->hb, P->db, P->lay, queries, P->Q, P->k.data(), P->off.data(), out_index, out_dist,
+                    out_count, &o, false, s, &nf);
+  if (st == FPS_OK && stats) {
+    stats->queries = P->Q;
+    stats->fallbacks = nf;
+    stats->path_used = P->learned ? FPS_PATH_LEARNED : (P->tc ? FPS_PATH_TC_FP8 : FPS_PATH_POPC_BATCH);
+  }
+  return st;
+}
+
+fps_status fps_batch_plan_release(fps_batch_plan plan) {
+  free_plan(reinterpret_cast<BatchPlan*>(plan));
   return FPS_OK;
 }
 

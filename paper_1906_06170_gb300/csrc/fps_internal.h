@@ -96,6 +96,7 @@ struct Library {
   std::mutex mu;
   std::map<cudaStream_t, Workspace*> ws;
   uint8_t* tc_fp8 = nullptr;     // 0/1 FP8 operand (tensor-core path), or null
+  std::map<int, int> tuned;      // autotuner: batch size class -> fastest batched path
 };
 
 // Per-query state of a batched search (device pointers; fps_batch.cu).

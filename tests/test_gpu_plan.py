@@ -1,0 +1,80 @@
+"""Graph-captured batch plans and the batched-path autotuner against the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def qstrs(p):
+    return synth.packed_to_strings(np.asarray(p).reshape(-1, 3))
+
+
+@pytest.mark.parametrize("path_name", ["POPC_BATCH", "TC_FP8"])
+def test_plan_runs_repeatedly_with_new_queries(gpu_lib, path_name):
+    fps = gpu_lib
+    n = 150000
+    text = synth.text(n, 81)
+    lib = fps.fps_library_load(text=text, flags=fps.FPS_LOAD_TC_OPERAND)
+    try:
+        ks = synth.k_mix(130, seed=81)
+        plan = fps.fps_batch_plan_create(lib, ks, path=getattr(fps, "FPS_PATH_" + path_name))
+        try:
+            for seed in (1081, 1082, 1083):
+                qs = synth.packed(len(ks), seed)
+                got = fps.fps_batch_plan_run(plan, qs)
+                want = oracle.topk_many(text, qstrs(qs), ks)
+                for (gi, gd), (wi, wd) in zip(got, want):
+                    assert np.array_equal(gi, wi) and np.array_equal(gd, wd)
+        finally:
+            fps.fps_batch_plan_release(plan)
+    finally:
+        fps.fps_release(lib)
+
+
+def test_learned_plan_and_fallback(gpu_lib):
+    fps = gpu_lib
+    n = 100000
+    text = synth.text(n, 82)
+    lib = fps.fps_library_load(text=text, flags=fps.FPS_LOAD_TC_OPERAND)
+    try:
+        ks = np.full(70, 30, np.int32)
+        qs = synth.packed(70, 1084)
+        want = oracle.topk_many(text, qstrs(qs), ks)
+        tk = np.array([w[1][-1] for w in want], np.float32)
+        plan = fps.fps_batch_plan_create(lib, ks, path=fps.FPS_PATH_TC_FP8, learned=True)
+        try:
+            for tau, nfall in ((tk, 0), (tk - 1.0, int(np.sum(tk > 0))), (tk + 3.0, 0)):
+                st = fps.fps_search_stats()
+                got = fps.fps_batch_plan_run(plan, qs, tau=tau, stats=st)
+                for (gi, gd), (wi, wd) in zip(got, want):
+                    assert np.array_equal(gi, wi) and np.array_equal(gd, wd)
+                assert st.fallbacks == nfall
+        finally:
+            fps.fps_batch_plan_release(plan)
+    finally:
+        fps.fps_release(lib)
+
+
+def test_autotuner_caches_a_choice_per_size_class(gpu_lib):
+    fps = gpu_lib
+    n = 300000
+    text = synth.text(n, 83)
+    lib = fps.fps_library_load(text=text, flags=fps.FPS_LOAD_TC_OPERAND)
+    try:
+        for nq in (3, 200):
+            seen = set()
+            for seed in (1085, 1086):
+                qs = synth.packed(nq, seed + nq)
+                ks = synth.k_mix(nq, seed=seed)
+                st = fps.fps_search_stats()
+                got = fps.fps_search_batch(lib, qs, ks, path=fps.FPS_PATH_AUTO, stats=st)
+                want = oracle.topk_many(text, qstrs(qs), ks)
+                for (gi, gd), (wi, wd) in zip(got, want):
+                    assert np.array_equal(gi, wi) and np.array_equal(gd, wd)
+                seen.add(st.path_used)
+            assert seen <= {fps.FPS_PATH_POPC_BATCH, fps.FPS_PATH_TC_FP8}
+    finally:
+        fps.fps_release(lib)

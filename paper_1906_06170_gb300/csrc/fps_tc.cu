@@ -5,32 +5,39 @@
 // so a batch of queries against the library is one dense contraction
 // Q x K x N (K = 166 keys, padded to 192) followed by a per-element compare.
 // Operands are 0/1 bytes in FP8 E4M3 (0x38 = 1.0, 0x00 = 0) and the
-// accumulators FP32.  Every product is 0 or 1 and every sum is an integer
-// <= 166, so the accumulator is the exact integer q . x (FP32 represents all
-// integers below 2^24); the distances equal the popcount path's.  (sm_103a has
-// no tcgen05 kind::i8, so there is no INT8 variant.)
+// accumulators FP16.  Every product is 0 or 1 and every partial sum an integer
+// <= 166, which FP16 represents exactly (all integers up to 2048), so the
+// accumulator is the exact integer q . x and the distances equal the popcount
+// path's.  (sm_103a has no tcgen05 kind::i8, so there is no INT8 variant.)
 //
-// CTA (one per SM, 6 warps):
+// CTA (one per SM, 12 warps):
 //   warp 0  producer: 1-D bulk copies (cp.async.bulk) of the query tile A
 //           (128 x 192 B, double-buffered per work item) and of library tiles B
 //           (256 x 192 B = 48 KB) into a 3-stage ring, completing on mbarriers;
 //   warp 1  allocates 512 TMEM columns; one thread issues 6 tcgen05.mma
 //           (kind::f8f6f4, K = 32 each) per library tile into one of two
-//           256-column FP32 accumulators and commits to the stage-free and
+//           256-column FP16 accumulators and commits to the stage-free and
 //           accumulator-full barriers;
-//   warp 10 drains the CTA's queue of accepted records into the per-query
-//           candidate regions (32 returning atomics per round trip), so the
-//           epilogue never waits on a global atomic;
 //   warps 2..9 epilogue: thread = query (TMEM lane), two warps per lane
-//           quarter, each reading 128 of the 256 columns with tcgen05.ld (two
-//           32-column loads per wait); it takes the max per 32 columns (3-input
-//           integer max on the non-negative FP32 bit patterns) and compares it
-//           with the query's threshold on the raw accumulator,
-//             d <= thr  <=>  acc >= (popc q + popc x - thr) / 2,
-//           which needs one number per (query, tile) because a tile lies inside
-//           one popcount bucket.  Records over the bar are appended to the
-//           query's candidate region and counted in its histogram (the shared
-//           batched state of fps_batch.cu), and the bound is re-derived.
+//           quarter, each reading 128 of the 256 columns with two tcgen05.ld
+//           (pack::16b: two FP16 columns per register) and one wait.  The
+//           accumulator goes back to the MMA as soon as the values are in
+//           registers.  The test needs one number per (query, tile), because a
+//           tile lies inside one popcount bucket:
+//             d <= thr  <=>  acc >= ceil((popc q + popc x - thr) / 2),
+//           taken as a 3-input max over the FP16 bit patterns (non-negative
+//           FP16 values order like unsigned integers) per 64 columns.  A lane
+//           whose 64 columns pass hands them, with the bar, to a shared ring;
+//   warp 10 flusher: finishes the compare of ring entries column by column
+//           (8 entries per round, 4 lanes per entry), takes candidate slots with
+//           one returning atomic per entry, appends (distance, position) to the
+//           query's candidate region, counts the query's histogram (the shared
+//           batched state of fps_batch.cu), and every 4 accepted records of a
+//           query asks for its bound to be re-derived;
+//   warp 11 refresher: re-derives a query's bound (smallest D with at least k
+//           accepted records at distance <= D) with a warp-wide prefix sum over
+//           its histogram and publishes it globally (atomicMin) and to the
+//           epilogue through a per-row shared word.
 // Operand layout (both operands, K-major, no swizzle): 8-row x 16-byte core
 // matrices of 128 contiguous bytes; along K they follow each other (leading
 // byte offset 128), along rows every 8-row group spans all 12 K-chunks (stride
@@ -39,6 +46,7 @@
 // Work: items (query tile, 64-tile library chunk) in chunk-major order, dealt
 // round-robin, so the 32 query tiles of a chunk run at the same time and the
 // chunk is read from HBM once and from L2 by the rest.
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -60,8 +68,10 @@ constexpr int kBStages = 3;
 constexpr int kChunkTiles = 64;              // library tiles per work item
 constexpr int kEpiWarps = 8;                 // two per TMEM lane quarter, 128 columns each
 constexpr int kFlushWarp = 2 + kEpiWarps;    // drains the candidate queue
-constexpr int kThreads = 32 * (3 + kEpiWarps);
-constexpr uint32_t kQueueCap = 1024;         // accepted records in flight per CTA
+constexpr int kRefWarp = 3 + kEpiWarps;      // re-derives query bounds from the histograms
+constexpr int kThreads = 32 * (4 + kEpiWarps);
+constexpr uint32_t kRefCap = 64;             // pending bound refreshes per CTA
+constexpr uint32_t kRingCap = 128;           // epilogue hand-offs in flight per CTA
 constexpr uint32_t kTmemCols = 512;
 
 // ------------------------------------------------------------------ PTX helpers
@@ -124,7 +134,7 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
 // (M >> 4 at bit 24).
 __device__ __forceinline__ uint32_t instr_desc() {
   uint32_t d = 0;
-  d |= 1u << 4;                           // D format: F32
+  d |= 0u << 4;                           // D format: F16
   d |= 0u << 7;                           // A format: E4M3
   d |= 0u << 10;                          // B format: E4M3
   d |= static_cast<uint32_t>(kTcRows >> 3) << 17;
@@ -145,11 +155,11 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                : "memory");
 }
 
-// 32 consecutive TMEM columns of this thread's lane (32x32b shape); the
-// registers are valid only after tmem_wait_ld().
-__device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t (&v)[32]) {
+// 64 consecutive 16-bit TMEM columns of this thread's lane, two per register
+// (pack::16b); valid only after tmem_wait_ld().
+__device__ __forceinline__ void tmem_ld64h_nowait(uint32_t taddr, uint32_t (&v)[32]) {
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "tcgen05.ld.sync.aligned.32x32b.x32.pack::16b.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
       "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
       : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
         "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
@@ -225,10 +235,17 @@ __global__ void tc_pack_queries_kernel(const uint64_t* q, int Q, uint8_t* op, in
 }
 
 // ------------------------------------------------------------------- scan
-// Accepted record waiting for the flusher; seq = queue slot + 1 once written.
-struct QEntry {
-  uint32_t q, d, pos, seq;
+// One epilogue lane's 64 FP16 accumulators (a query against 64 records) that
+// passed the tile-level test, with what the flusher needs to finish the compare:
+//   m0 = need (FP16 bit pattern) | valid columns << 16,
+//   m1 = popc q + popc x | item sequence << 9,  pos0 = layout position of column 0;
+// seq = ring slot + 1 once written.
+struct RingEntry {
+  uint4 v[8];
+  uint32_t q, m0, m1, pos0;
+  uint32_t seq, pad[3];
 };
+static_assert(sizeof(RingEntry) == 160, "ring entry layout");
 
 struct TcSmem {
   uint8_t a[2][kATileBytes];
@@ -240,59 +257,37 @@ struct TcSmem {
   uint32_t tmem_base;
   int tile_off2[kNumBuckets + 1];  // first tensor tile of each bucket
   int bcount[kNumBuckets + 1];
-  QEntry queue[kQueueCap];
-  uint32_t q_tail;                 // slots claimed by the epilogue
-  uint32_t q_head;                 // slots retired by the flusher
+  RingEntry ring[kRingCap];
+  // per query row: (item sequence << 32) | ~bound -- a 64-bit max keeps the newest
+  // item and, within it, the smallest bound
+  unsigned long long thr_w[kTcQ];
+  uint32_t pend[kTcQ];             // accepted records per row (refresh every 4)
+  uint2 ref_q[kRefCap];            // refresh requests (query, item sequence)
+  uint32_t r_tail;                 // ring slots claimed by the epilogue
+  uint32_t r_head;                 // ring slots retired by the flusher
   uint32_t epi_done;               // epilogue warps finished
+  uint32_t ref_tail;               // refresh requests posted (flusher)
+  uint32_t ref_head;               // refresh requests done (refresher)
+  uint32_t flush_done;             // flusher finished
 };
+static_assert(sizeof(TcSmem) + 1024 <= 232448, "shared memory per CTA");
 
-// Epilogue side: claim a queue slot, wait (bounded) for room, write the entry.
-// Out of line: it runs rarely and must not bloat the unrolled accumulator scan.
-__device__ __noinline__ bool queue_push(TcSmem& S, uint32_t q, uint32_t d, uint32_t pos, uint64_t timeout_ns) {
-  const uint32_t slot = atomicAdd(&S.q_tail, 1u);
-  if (slot - *reinterpret_cast<volatile uint32_t*>(&S.q_head) >= kQueueCap) {
+// Epilogue side: claim a ring slot, wait (bounded) for room, write the entry.
+__device__ __forceinline__ bool ring_push(TcSmem& S, const uint32_t (&w)[32], uint32_t q, uint32_t m0, uint32_t m1,
+                                          uint32_t pos0, uint64_t timeout_ns) {
+  const uint32_t slot = atomicAdd(&S.r_tail, 1u);
+  if (slot - *reinterpret_cast<volatile uint32_t*>(&S.r_head) >= kRingCap) {
     const uint64_t deadline = global_ns() + timeout_ns;
-    while (slot - *reinterpret_cast<volatile uint32_t*>(&S.q_head) >= kQueueCap)
+    while (slot - *reinterpret_cast<volatile uint32_t*>(&S.r_head) >= kRingCap)
       if (global_ns() > deadline) return false;
   }
-  QEntry& e = S.queue[slot % kQueueCap];
-  e.q = q;
-  e.d = d;
-  e.pos = pos;
+  RingEntry& e = S.ring[slot % kRingCap];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) e.v[i] = make_uint4(w[4 * i], w[4 * i + 1], w[4 * i + 2], w[4 * i + 3]);
+  *reinterpret_cast<uint4*>(&e.q) = make_uint4(q, m0, m1, pos0);
   __threadfence_block();
   *reinterpret_cast<volatile uint32_t*>(&e.seq) = slot + 1;
   return true;
-}
-
-// Smallest D <= thr with at least k counts in hist[0..D], else 167.  The first
-// 48 bins are fetched in one round trip; larger bounds continue 8 bins at a time.
-__device__ __forceinline__ uint32_t bound_of(const uint32_t* hist, uint32_t thr, int k) {
-  uint32_t run = 0;
-  uint32_t h[48];
-#pragma unroll
-  for (int e = 0; e < 48; e += 2) {
-    uint2 v = __ldcg(reinterpret_cast<const uint2*>(hist + e));
-    h[e] = v.x;
-    h[e + 1] = v.y;
-  }
-#pragma unroll
-  for (int e = 0; e < 48; ++e) {
-    if (static_cast<uint32_t>(e) > thr) return 167u;
-    run += h[e];
-    if (run >= static_cast<uint32_t>(k)) return static_cast<uint32_t>(e);
-  }
-  for (uint32_t base = 48; base <= thr; base += 8) {
-    uint32_t h8[8];
-#pragma unroll
-    for (int e = 0; e < 8; ++e) h8[e] = (base + e <= thr) ? __ldcg(hist + base + e) : 0u;
-#pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      if (base + e > thr) return 167u;
-      run += h8[e];
-      if (run >= static_cast<uint32_t>(k)) return base + e;
-    }
-  }
-  return 167u;
 }
 
 // Bucket of tensor tile T (tiles of one bucket are contiguous).
@@ -333,12 +328,19 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&S.acc_empty[i], kEpiWarps);
     }
     mbar_init(&S.fin, 1);
-    S.q_tail = 0;
-    S.q_head = 0;
+    S.r_tail = 0;
+    S.r_head = 0;
     S.epi_done = 0;
+    S.ref_tail = 0;
+    S.ref_head = 0;
+    S.flush_done = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  for (uint32_t i = threadIdx.x; i < kQueueCap; i += blockDim.x) S.queue[i].seq = 0;
+  for (uint32_t i = threadIdx.x; i < kRingCap; i += blockDim.x) S.ring[i].seq = 0;
+  for (int i = threadIdx.x; i < kTcQ; i += blockDim.x) {
+    S.thr_w[i] = 0ull;
+    S.pend[i] = 0u;
+  }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&S.tmem_base)),
                  "r"(kTmemCols)
@@ -458,116 +460,73 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int64_t c = item / n_qt;
       const int q = qt * kTcQ + row;
       const bool live = q < b.Q && b.k[q] > 0;
-      const int kq = live ? b.k[q] : 0;
       int pq = 0;
       uint32_t thr = 0;
-      uint32_t* hq = nullptr;
+      const unsigned long long jkey = static_cast<unsigned long long>(j) << 32;
       if (live) {
         pq = __popcll(b.queries[3 * q]) + __popcll(b.queries[3 * q + 1]) + __popcll(b.queries[3 * q + 2]);
         thr = ld_relaxed_u32(b.thr + q);
-        hq = b.hist + static_cast<size_t>(q) * 168;
+        atomicMax(&S.thr_w[row], jkey | (0xFFFFFFFFu - thr));
       }
-      uint32_t pending = 0;                        // accepted since the last bound refresh
-      const uint32_t refresh_at = 4u;
-      bool refresh = false;                        // histogram bins requested for this tile
-      uint32_t hb[48];
       const int64_t t0 = c * kChunkTiles, t1 = min(t0 + kChunkTiles, n_tc);
       bk = bucket_of(S.tile_off2, t0);
       for (int64_t T = t0; T < t1; ++T, ++tn) {
         const int acc = static_cast<int>(tn & 1);
+        if (live) {   // the refresher may have tightened this row's bound
+          const unsigned long long w = *reinterpret_cast<volatile unsigned long long*>(&S.thr_w[row]);
+          if ((w >> 32) == static_cast<unsigned long long>(j)) {
+            const uint32_t t = 0xFFFFFFFFu - static_cast<uint32_t>(w);
+            thr = t < thr ? t : thr;
+          }
+        }
         while (bk + 1 < kNumBuckets && S.tile_off2[bk + 1] <= T) ++bk;
         int nvalid = S.bcount[bk] - static_cast<int>(T - S.tile_off2[bk]) * kTcRows;
         nvalid = nvalid < kTcRows ? nvalid : kTcRows;
         const bool act = live && static_cast<uint32_t>(abs(bk - pq)) <= thr;
         // acc >= (pq + px - thr) / 2  <=>  d <= thr;  twice the bar keeps it an integer
         const int bar2 = pq + bk - static_cast<int>(thr);
-        if (live && pending > 0 && T + 1 == t1) refresh = true;   // last tile: refresh before the query tile changes
-        if (refresh) {
-          // issue the histogram loads now; they are consumed after this tile's work
-#pragma unroll
-          for (int e = 0; e < 48; e += 2) {
-            uint2 v = __ldcg(reinterpret_cast<const uint2*>(hq + e));
-            hb[e] = v.x;
-            hb[e + 1] = v.y;
-          }
-        }
         const bool landed = mbar_wait(&S.acc_full[acc], (tn >> 1) & 1, deadline);
         if (!__all_sync(kFull, landed)) {   // one verdict for the whole warp
           ok = false;
           break;
         }
         tc_fence_after();
-        if (__any_sync(kFull, act)) {
-          for (int ch = 0; ch < 4; ch += 2) {
-            uint32_t v[2][32];
-            const uint32_t col0 = static_cast<uint32_t>(acc * kTcRows + half * 128 + ch * 32);
-            __syncwarp();   // warp-collective loads: reconverge lanes that skipped the previous chunk
-            tmem_ld32_nowait(tmem + lane_addr + col0, v[0]);
-            tmem_ld32_nowait(tmem + lane_addr + col0 + 32, v[1]);
-            tmem_wait_ld();
-            if (!act) continue;
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              // FP32 values here are non-negative integers: their bit patterns order like ints
-              int m = __vimax3_s32(static_cast<int>(v[h][0]), static_cast<int>(v[h][1]), static_cast<int>(v[h][2]));
-#pragma unroll
-              for (int e = 3; e < 31; e += 2) m = __vimax3_s32(m, static_cast<int>(v[h][e]), static_cast<int>(v[h][e + 1]));
-              m = max(m, static_cast<int>(v[h][31]));
-              if (2 * static_cast<int>(__int_as_float(m)) < bar2) continue;
-              // rare: some record of these 32 is within the bound.  Mark the passing
-              // columns, then take them one by one (a select chain reads v[e] without
-              // indexing registers dynamically).
-              const int colb = half * 128 + (ch + h) * 32;
-              uint32_t mask = 0;
-#pragma unroll
-              for (int e = 0; e < 32; ++e)
-                mask |= static_cast<uint32_t>(2 * static_cast<int>(__uint_as_float(v[h][e])) >= bar2 &&
-                                              colb + e < nvalid) << e;
-              while (mask) {
-                const int e0 = __ffs(mask) - 1;
-                mask &= mask - 1;
-                uint32_t raw = 0;
-#pragma unroll
-                for (int e = 0; e < 32; ++e) raw = (e == e0) ? v[h][e] : raw;
-                const int a = static_cast<int>(__uint_as_float(raw));
-                const uint32_t d = static_cast<uint32_t>(pq + bk - 2 * a);
-                const uint32_t pos = static_cast<uint32_t>(T * kTcRows + colb + e0);
-                red_add_u32(hq + d, 1u);
-                if (!queue_push(S, static_cast<uint32_t>(q), d, pos, deadline)) ok = false;
-                ++pending;
-              }
-            }
-          }
+        uint32_t v[2][32];
+        const bool any_act = __any_sync(kFull, act);
+        if (any_act) {
+          const uint32_t col0 = static_cast<uint32_t>(acc * kTcRows + half * 128);
+          tmem_ld64h_nowait(tmem + lane_addr + col0, v[0]);
+          tmem_ld64h_nowait(tmem + lane_addr + col0 + 64, v[1]);
+          tmem_wait_ld();
         }
+        // the values are in registers: hand the accumulator back to the MMA before comparing
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&S.acc_empty[acc]);
-        // tighten this query's bound from the bins fetched during this tile
-        if (refresh) {
-          refresh = false;
-          uint32_t run = 0, D = 167u;
+        if (act) {
+          // acc >= ceil(bar2 / 2); non-negative FP16 bit patterns order like unsigned ints
+          const int need = (bar2 + 1) >> 1;
+          const uint32_t need16 = need <= 0 ? 0u : static_cast<uint32_t>(__half_as_ushort(__int2half_rn(need)));
+          auto group = [&](const uint32_t (&w)[32], int g) {
+            uint32_t m = __vimax3_u16x2(w[0], w[1], w[2]);
 #pragma unroll
-          for (int e = 0; e < 48; ++e) {
-            run += hb[e];
-            if (D == 167u && run >= static_cast<uint32_t>(kq) && static_cast<uint32_t>(e) <= thr) D = e;
-          }
-          if (D < thr) {
-            thr = D;
-            atomicMin(b.thr + q, D);
-          }
+            for (int e = 3; e < 31; e += 2) m = __vimax3_u16x2(m, w[e], w[e + 1]);
+            m = __vmaxu2(m, w[31]);
+            if (max(m & 0xFFFFu, m >> 16) < need16) return;
+            // rare: some of these 64 records may be within the bound; the flusher
+            // finishes the compare column by column
+            const int colb = half * 128 + g * 64;
+            int lim = nvalid - colb;
+            lim = lim < 64 ? lim : 64;
+            if (lim <= 0) return;
+            if (!ring_push(S, w, static_cast<uint32_t>(q), need16 | (static_cast<uint32_t>(lim) << 16),
+                           static_cast<uint32_t>(pq + bk) | (static_cast<uint32_t>(j) << 9),
+                           static_cast<uint32_t>(T * kTcRows + colb), deadline))
+              ok = false;
+          };
+          group(v[0], 0);
+          group(v[1], 1);
         }
-        if (live && pending >= refresh_at) {   // request a refresh for the next tile
-          pending = 0;
-          refresh = true;
-        }
-        if (live && ((T - t0) & 15) == 15) {
-          uint32_t g = ld_relaxed_u32(b.thr + q);
-          thr = g < thr ? g : thr;
-        }
-      }
-      if (live && refresh) {  // a refresh was due at the item's end: do it before the query tile changes
-        const uint32_t D = bound_of(hq, thr, kq);
-        if (D < thr) atomicMin(b.thr + q, D);
       }
       if (!ok) break;
     }
@@ -576,16 +535,20 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) atomicAdd(&S.epi_done, 1u);
   } else if (warp == kFlushWarp) {
     // ---------------------------------------------------------------- flusher
-    uint32_t head = 0;
+    // Up to 8 ring entries per round, 4 lanes per entry (8 registers = 16 columns
+    // each): exact compare, one returning atomic per entry for candidate slots,
+    // histogram counts, and a bound refresh request every 4 accepted records.
+    uint32_t head = 0, rtail = 0;
     uint64_t idle_since = 0;
+    const int g = lane >> 2, sub = lane & 3;
     for (;;) {
-      const uint32_t idx = head + lane;
-      const bool ready = *reinterpret_cast<volatile uint32_t*>(&S.queue[idx % kQueueCap].seq) == idx + 1;
-      const uint32_t bal = __ballot_sync(kFull, ready);
-      const int n = bal == kFull ? 32 : __ffs(~bal) - 1;   // ready entries in a row from head
+      const uint32_t idx = head + static_cast<uint32_t>(lane & 7);
+      const bool ready = *reinterpret_cast<volatile uint32_t*>(&S.ring[idx % kRingCap].seq) == idx + 1;
+      const uint32_t bal = __ballot_sync(kFull, ready) & 0xFFu;
+      const int n = bal == 0xFFu ? 8 : __ffs(~bal) - 1;   // ready entries in a row from head
       if (n == 0) {
         const bool epi_over = *reinterpret_cast<volatile uint32_t*>(&S.epi_done) == kEpiWarps;
-        if (epi_over && *reinterpret_cast<volatile uint32_t*>(&S.q_tail) == head) break;
+        if (epi_over && *reinterpret_cast<volatile uint32_t*>(&S.r_tail) == head) break;
         // idle: wait for the epilogue (itself bounded); claimed-but-unwritten slots after
         // it finished get timeout_ns, and no idle spell may exceed 32 x timeout_ns
         const uint64_t now = global_ns();
@@ -594,20 +557,146 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (lane == 0) atomicOr(b.err, DEVERR_TIMEOUT);
           break;
         }
-        __nanosleep(256);
+        __nanosleep(128);
         continue;
       }
       idle_since = 0;
       __threadfence_block();
-      if (lane < n) {
-        const QEntry& e = S.queue[idx % kQueueCap];
-        const int64_t off = b.cand_off[e.q], cap = b.cand_off[e.q + 1] - off;
-        const uint32_t slot = atomicAdd(b.cnt + e.q, 1u);
-        if (slot < cap) b.cand[off + slot] = (static_cast<unsigned long long>(e.d) << 32) | e.pos;
+      const bool mine = g < n;
+      const RingEntry& e = S.ring[(head + static_cast<uint32_t>(g)) % kRingCap];
+      uint32_t eq = 0, m0 = 0, m1 = 0, pos0 = 0;
+      uint32_t w[8];
+      if (mine) {
+        const uint4 mt = *reinterpret_cast<const uint4*>(&e.q);
+        eq = mt.x;
+        m0 = mt.y;
+        m1 = mt.z;
+        pos0 = mt.w;
+        const uint4 a0 = e.v[2 * sub], a1 = e.v[2 * sub + 1];
+        w[0] = a0.x; w[1] = a0.y; w[2] = a0.z; w[3] = a0.w;
+        w[4] = a1.x; w[5] = a1.y; w[6] = a1.z; w[7] = a1.w;
+      }
+      const uint32_t need16 = m0 & 0xFFFFu, need2 = need16 | (need16 << 16);
+      const int lim = static_cast<int>(m0 >> 16);
+      // halves are below 0x8000: (w | 0x80008000) - need2 borrows across neither half and
+      // leaves bit 15 (31) set exactly where the low (high) half is >= need
+      uint32_t hits = 0;   // bit i: column 16 sub + i passes
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const uint32_t t = ((w[r] | 0x80008000u) - need2) & 0x80008000u;
+        hits |= ((t >> 15) & 1u) << (2 * r);
+        hits |= (t >> 31) << (2 * r + 1);
+      }
+      const int c0 = 16 * sub;
+      if (!mine || lim <= c0) hits = 0;
+      else if (lim < c0 + 16) hits &= (1u << (lim - c0)) - 1u;
+      const uint32_t cnt = __popc(hits);
+      // exclusive prefix of the counts over the 4 lanes of this entry
+      uint32_t incl = cnt;
+      {
+        const uint32_t y1 = __shfl_up_sync(kFull, incl, 1);
+        if (sub >= 1) incl += y1;
+        const uint32_t y2 = __shfl_up_sync(kFull, incl, 2);
+        if (sub >= 2) incl += y2;
+      }
+      const uint32_t total = __shfl_sync(kFull, incl, (lane & ~3) + 3);
+      uint32_t base = 0;
+      bool req = false;
+      if (mine && sub == 0 && total > 0) {
+        base = atomicAdd(b.cnt + eq, total);
+        const uint32_t old = atomicAdd(&S.pend[eq % kTcQ], total);
+        req = (old >> 2) != ((old + total) >> 2);
+      }
+      base = __shfl_sync(kFull, base, lane & ~3);
+      if (hits) {
+        const int64_t off = b.cand_off[eq], cap = b.cand_off[eq + 1] - off;
+        uint32_t slot = base + incl - cnt;
+        uint32_t* hq = b.hist + static_cast<size_t>(eq) * 168;
+        const int dbase = static_cast<int>(m1 & 0x1FFu);
+        while (hits) {
+          const int i = __ffs(hits) - 1;
+          hits &= hits - 1;
+          uint32_t x = 0;
+#pragma unroll
+          for (int r = 0; r < 8; ++r) x |= w[r] & (0u - static_cast<uint32_t>(r == (i >> 1)));
+          const uint32_t h16 = (i & 1) ? (x >> 16) : (x & 0xFFFFu);
+          const int a = static_cast<int>(__half2float(__ushort_as_half(static_cast<unsigned short>(h16))));
+          const uint32_t d = static_cast<uint32_t>(dbase - 2 * a);
+          red_add_u32(hq + d, 1u);
+          if (slot < cap) b.cand[off + slot] = (static_cast<unsigned long long>(d) << 32) | (pos0 + c0 + i);
+          ++slot;
+        }
       }
       __syncwarp();
-      head += n;
-      if (lane == 0) *reinterpret_cast<volatile uint32_t*>(&S.q_head) = head;
+      head += static_cast<uint32_t>(n);
+      if (lane == 0) *reinterpret_cast<volatile uint32_t*>(&S.r_head) = head;
+      // post refresh requests while there is room (a dropped request only delays a bound)
+      const uint32_t rb = __ballot_sync(kFull, req);
+      if (rb) {
+        uint32_t rh = 0;
+        if (lane == 0) rh = *reinterpret_cast<volatile uint32_t*>(&S.ref_head);
+        const uint32_t room = kRefCap - (rtail - __shfl_sync(kFull, rh, 0));   // one view for the warp
+        const uint32_t rank = __popc(rb & ((1u << lane) - 1u));
+        if (req && rank < room) S.ref_q[(rtail + rank) % kRefCap] = make_uint2(eq, m1 >> 9);
+        const uint32_t posted = min(static_cast<uint32_t>(__popc(rb)), room);
+        __threadfence_block();
+        __syncwarp();
+        rtail += posted;
+        if (lane == 0) *reinterpret_cast<volatile uint32_t*>(&S.ref_tail) = rtail;
+      }
+    }
+    __syncwarp();
+    if (lane == 0) *reinterpret_cast<volatile uint32_t*>(&S.flush_done) = 1u;
+  } else if (warp == kRefWarp) {
+    // -------------------------------------------------------------- refresher
+    // bound = smallest D <= thr with at least k accepted records at distance <= D,
+    // from the query's histogram (any subset of its counts gives a valid bound)
+    uint32_t rhead = 0;
+    uint64_t idle_since = 0;
+    for (;;) {
+      const uint32_t rt = *reinterpret_cast<volatile uint32_t*>(&S.ref_tail);
+      if (rt == rhead) {
+        const bool fl_over = *reinterpret_cast<volatile uint32_t*>(&S.flush_done) != 0u;
+        if (fl_over && *reinterpret_cast<volatile uint32_t*>(&S.ref_tail) == rhead) break;
+        const uint64_t now = global_ns();
+        if (idle_since == 0) idle_since = now;
+        if (now - idle_since > 64 * timeout_ns) {
+          if (lane == 0) atomicOr(b.err, DEVERR_TIMEOUT);
+          break;
+        }
+        __nanosleep(512);
+        continue;
+      }
+      idle_since = 0;
+      __threadfence_block();
+      const uint2 r = S.ref_q[rhead % kRefCap];
+      const uint32_t rq = r.x, rj = r.y;
+      const uint32_t kq = static_cast<uint32_t>(b.k[rq]);
+      const uint32_t tcur = ld_relaxed_u32(b.thr + rq);
+      const uint32_t* hist = b.hist + static_cast<size_t>(rq) * 168;
+      uint32_t carry = 0, D = 167u;
+      for (uint32_t base = 0; base <= tcur && base < 168u; base += 32) {
+        const uint32_t e = base + lane;
+        uint32_t x = (e <= tcur && e < 168u) ? __ldcg(hist + e) : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t y = __shfl_up_sync(kFull, x, o);
+          if (lane >= o) x += y;
+        }
+        const uint32_t hit = __ballot_sync(kFull, e <= tcur && carry + x >= kq);
+        if (hit) {
+          D = base + static_cast<uint32_t>(__ffs(hit) - 1);
+          break;
+        }
+        carry += __shfl_sync(kFull, x, 31);
+      }
+      if (lane == 0 && D < tcur) {
+        atomicMin(b.thr + rq, D);
+        atomicMax(&S.thr_w[rq % kTcQ], (static_cast<unsigned long long>(rj) << 32) | (0xFFFFFFFFu - D));
+      }
+      __syncwarp();
+      ++rhead;
+      if (lane == 0) *reinterpret_cast<volatile uint32_t*>(&S.ref_head) = rhead;
     }
   }
 

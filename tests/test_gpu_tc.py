@@ -1,7 +1,9 @@
 """Parity of the tensor-core batched path (tcgen05, FP8 0/1 operands) with the CPU oracle.
 
-The contraction is exact (0/1 products, integer sums <= 166 in FP32), so the
-results must equal the oracle's element by element.
+The contraction is exact (0/1 products, integer sums <= 166, which the FP16
+accumulators represent exactly), so the results must equal the oracle's
+element by element.  The ties case (20,000 identical records) drives many
+accepted records through the epilogue's hand-off ring at once.
 """
 import numpy as np
 import pytest

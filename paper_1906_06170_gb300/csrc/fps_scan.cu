@@ -47,12 +47,15 @@ constexpr int kThrBytes = 16;
 // out one by one, still in sweep order, by kQueues counters on separate cache
 // lines (warp w draws from counter w % kQueues), so warps the memory system
 // serves faster take more of the tail.  Each warp keeps two requests in flight
-// so the atomics' latency stays hidden.
-constexpr int kStaticNum = 3, kStaticDen = 4;
+// so the atomics' latency stays hidden.  Some SMs stream up to ~40% slower
+// than the rest; their static share must end before the tail runs out, while
+// tail items cost a little more than static ones: 5/8 static measured best.
+constexpr int kStaticNum = 5, kStaticDen = 8;
 constexpr int kQueues = 16;
 constexpr int kStageBytes = kTileBytes + kThrBytes;
 constexpr int kTieCap = 16384;          // tie keys sorted in shared memory by the merge
 constexpr int kFinCap = 2048;           // >= FPS_K_MAX, power of two
+constexpr int kWarpSortMax = 256;       // merge sorts up to this many keys in one warp
 
 // ------------------------------------------------------------------ PTX helpers
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -628,18 +631,32 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
   int* hs = tb.lo_b;  // reuse: 167 ints
   for (int b = tid; b < kNumBuckets; b += blockDim.x) hs[b] = static_cast<int>(ld_relaxed_u32(&st->hist[b]));
   __syncthreads();
-  if (tid == 0) {
-    long long run = 0;
-    int T = kNumBuckets;
-    for (int b = 0; b < kNumBuckets; ++b) {
-      if (run + hs[b] >= k_eff) {
-        T = b;
+  if (warp == 0) {
+    // T = first distance whose running count reaches k_eff (warp prefix sums, 32 bins a round)
+    uint32_t carry = 0;
+    int T = kNumBuckets, cl = 0;
+    for (int c0 = 0; c0 < kNumBuckets; c0 += 32) {
+      const int b = c0 + lane;
+      const uint32_t v = b < kNumBuckets ? static_cast<uint32_t>(hs[b]) : 0u;
+      uint32_t incl = v;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const uint32_t hit = __ballot_sync(kFull, b < kNumBuckets && carry + incl >= static_cast<uint32_t>(k_eff));
+      if (hit) {
+        const int f = __ffs(hit) - 1;
+        T = c0 + f;
+        cl = static_cast<int>(carry + __shfl_sync(kFull, incl - v, f));
         break;
       }
-      run += hs[b];
+      carry += __shfl_sync(kFull, incl, 31);
     }
-    tb.T = T;
-    tb.cless = static_cast<int>(run);
+    if (lane == 0) {
+      tb.T = T;
+      tb.cless = T < kNumBuckets ? cl : static_cast<int>(carry);
+    }
   }
   __syncthreads();
   const uint32_t T = static_cast<uint32_t>(tb.T);
@@ -662,12 +679,22 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
   const int ntie = tb.ntie;
   if (need > 0) {
     if (ntie <= kTieCap) {
-      int p = next_pow2(ntie);
-      for (int i = ntie + tid; i < p; i += blockDim.x) ties[i] = ~0ull;
-      __syncthreads();
-      block_bitonic_sort(ties, p);
-      for (int i = tid; i < need; i += blockDim.x)
-        if (cless + i < kFinCap) fin[cless + i] = ties[i];
+      const int p = next_pow2(ntie);
+      if (p <= kWarpSortMax) {   // few ties: one warp sorts them, no block-wide barriers
+        if (warp == 0) {
+          for (int i = ntie + lane; i < p; i += 32) ties[i] = ~0ull;
+          __syncwarp();
+          warp_bitonic_sort(ties, p, lane);
+          for (int i = lane; i < need; i += 32)
+            if (cless + i < kFinCap) fin[cless + i] = ties[i];
+        }
+      } else {
+        for (int i = ntie + tid; i < p; i += blockDim.x) ties[i] = ~0ull;
+        __syncthreads();
+        block_bitonic_sort(ties, p);
+        for (int i = tid; i < need; i += blockDim.x)
+          if (cless + i < kFinCap) fin[cless + i] = ties[i];
+      }
     } else {
       // Many equal distances: find the need-th smallest index at distance T by bisection.
       __shared__ int s_cnt;
@@ -702,15 +729,28 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
   }
   __syncthreads();
   {
-    int p = next_pow2(k_eff);
-    for (int i = k_eff + tid; i < p; i += blockDim.x) fin[i] = ~0ull;
-    __syncthreads();
-    block_bitonic_sort(fin, p);
-    for (int i = tid; i < k_eff; i += blockDim.x) {
-      out_idx[i] = static_cast<int32_t>(fin[i] & 0xFFFFFFFFull);
-      out_dist[i] = static_cast<int32_t>(fin[i] >> 32);
+    const int p = next_pow2(k_eff);
+    if (p <= kWarpSortMax) {
+      if (warp == 0) {
+        for (int i = k_eff + lane; i < p; i += 32) fin[i] = ~0ull;
+        __syncwarp();
+        warp_bitonic_sort(fin, p, lane);
+        for (int i = lane; i < k_eff; i += 32) {
+          out_idx[i] = static_cast<int32_t>(fin[i] & 0xFFFFFFFFull);
+          out_dist[i] = static_cast<int32_t>(fin[i] >> 32);
+        }
+        if (lane == 0) *out_count = k_eff;
+      }
+    } else {
+      for (int i = k_eff + tid; i < p; i += blockDim.x) fin[i] = ~0ull;
+      __syncthreads();
+      block_bitonic_sort(fin, p);
+      for (int i = tid; i < k_eff; i += blockDim.x) {
+        out_idx[i] = static_cast<int32_t>(fin[i] & 0xFFFFFFFFull);
+        out_dist[i] = static_cast<int32_t>(fin[i] >> 32);
+      }
+      if (tid == 0) *out_count = k_eff;
     }
-    if (tid == 0) *out_count = k_eff;
   }
   // restore the scan state for the next search on this workspace
   for (int b = tid; b < 168; b += blockDim.x) st->hist[b] = 0u;

@@ -49,7 +49,7 @@ def parse_args():
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--n", type=int, default=PAPER_N, help="library records")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--workload", default="single", choices=["single", "batch", "learned", "serve"],
+    p.add_argument("--workload", default="single", choices=["single", "batch", "learned", "serve", "latency"],
                    help="single: 16 sequential single queries per step (default); "
                         "batch: --queries queries with mixed k in one batched call per step")
     p.add_argument("--queries", type=int, default=4096)
@@ -156,9 +156,35 @@ def cpu_oracle_throughput(records: int, nq: int, seconds_hint: str):
     for q in qs:
         oracle.topk(text, q, K, threads=threads)
     dt = time.perf_counter() - t0
+    # the distance step alone (parse + character compares, all threads) on two of the queries;
+    # the rest of a query's time is the full sort of its N (distance, index) pairs
+    nd = min(2, nq)
+    t1 = time.perf_counter()
+    for q in qs[:nd]:
+        oracle.distances(text, q, threads=threads)
+    dist_s = (time.perf_counter() - t1) / nd
+    per_q = dt / nq
     return {"value": records * nq / dt / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"{nq} queries x {records:,} records of the same generator (parse + distances on "
-                      f"{threads} threads + full sort), {dt:.1f} s{seconds_hint}"}
+                      f"{threads} threads + full sort), {dt:.1f} s{seconds_hint}",
+            "split_s_per_query": {"distances": dist_s, "sort": max(per_q - dist_s, 0.0)},
+            "paper_method_context": paper_method_context()}
+
+
+def paper_method_context(records: int = 50_000):
+    """The paper's own search (Fig. 3, NumPy broadcast over the parsed text, one thread) on a bounded
+    chunk, extrapolated to 95,417,114 records as context beside the paper's ~40 min (Sec. 2.2)."""
+    import oracle
+    import synth
+
+    rows = synth.packed_to_strings(synth.packed(records, 0))
+    q = synth.packed_to_strings(synth.packed(1, 1001))[0]
+    t0 = time.perf_counter()
+    oracle.fig3_topk(rows, q, K)
+    dt = time.perf_counter() - t0
+    return {"value": records / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "paper method (Fig. 3, NumPy)",
+            "sample": f"1 query x {records:,} records, {dt:.2f} s",
+            "extrapolated_s_at_95M": dt * PAPER_N / records}
 
 
 # -------------------------------------------------------------- reference
@@ -213,18 +239,17 @@ def run_gb300(args):
     del packed
     qs = synth.packed(QUERIES_PER_STEP * ws, 1001)[rank * QUERIES_PER_STEP:(rank + 1) * QUERIES_PER_STEP]
     qd = torch.from_numpy(qs.view(np.int64).copy()).to(dev)
-    oi = torch.empty((QUERIES_PER_STEP, K), dtype=torch.int32, device=dev)
-    od = torch.empty((QUERIES_PER_STEP, K), dtype=torch.int32, device=dev)
+    ks = np.full(QUERIES_PER_STEP, K, np.int32)
+    off = fps.batch_offsets(ks)
+    oi = torch.empty(QUERIES_PER_STEP * K, dtype=torch.int32, device=dev)
+    od = torch.empty(QUERIES_PER_STEP * K, dtype=torch.int32, device=dev)
     oc = torch.empty((QUERIES_PER_STEP,), dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
 
-    def step(events=None):
-        for j in range(QUERIES_PER_STEP):
-            if events is not None:
-                events[2 * j].record(stream)
-            fps.fps_search_packed(lib, qd[j], K, out_index=oi[j], out_dist=od[j], out_count=oc[j], stream=stream)
-            if events is not None:
-                events[2 * j + 1].record(stream)
+    def step():
+        # the 16 queries one after another through the single-query scan (each streams the whole library)
+        fps.fps_search_batch(lib, qd, ks, path=fps.FPS_PATH_POPC, out_index=oi, out_dist=od, out_count=oc,
+                             offsets=off, stream=stream)
 
     for _ in range(args.warmup):
         step()
@@ -238,21 +263,17 @@ def run_gb300(args):
     # ---- timed region (device-resident inputs and outputs)
     clocks = ClockSampler(local)
     clocks.start()
-    per_launch = [[torch.cuda.Event(enable_timing=True) for _ in range(2 * QUERIES_PER_STEP)]
-                  for _ in range(args.steps)]
     barrier()
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
     t_start.record(stream)
     for s in range(args.steps):
-        step(per_launch[s])
+        step()
     t_end.record(stream)
     barrier()
     clk = clocks.stop()
     fps.fps_sync(lib, stream)
     ms = t_start.elapsed_time(t_end)
-    launch_ms = [per_launch[s][2 * j].elapsed_time(per_launch[s][2 * j + 1])
-                 for s in range(args.steps) for j in range(QUERIES_PER_STEP)]
     if ws > 1:
         t = torch.tensor([ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -260,7 +281,7 @@ def run_gb300(args):
 
     # sanity of the last step's results (full parity is in the test suite)
     cnt = oc.cpu().numpy()
-    dd = od.cpu().numpy()
+    dd = od.cpu().numpy().reshape(QUERIES_PER_STEP, K)
     assert np.all(cnt == min(K, n)) and np.all(np.diff(dd, axis=1) >= 0), "bench results malformed"
 
     # ---- end to end through the C ABI with host buffers (copies inside the timed region)
@@ -269,8 +290,7 @@ def run_gb300(args):
     barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        for j in range(QUERIES_PER_STEP):
-            fps.fps_search_packed(lib, qs_host[j], K)
+        fps.fps_search_batch(lib, qs_host, ks, path=fps.FPS_PATH_POPC)
     barrier()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     if ws > 1:
@@ -292,12 +312,15 @@ def run_gb300(args):
             lo, hi = int(max(0, pq[j] - tk[j])), int(min(166, pq[j] + tk[j]))
             alg.append(24.0 * bc[lo:hi + 1].sum() + 8.0 * K)
         alg_bytes = float(np.mean(alg))
-        avg_launch_s = float(np.mean(launch_ms)) / 1e3
+        # one query's share of the step: the 16 launches run back to back, each overlapping
+        # only its start with the previous query's merge
+        avg_launch_s = ms / args.steps / QUERIES_PER_STEP / 1e3
         peak, peak_kind = measured_peak_gbs()
         achieved = alg_bytes / avg_launch_s / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": profile_traffic(), "kernel": "scan_single_kernel<16,256>",
                 "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_launch_s * 1e3,
+                "avg_launch_basis": "timed step / 16 queries (CUDA events on the launching stream)",
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                 else "fallback 6.8 TB/s"}
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -314,8 +337,8 @@ def run_gb300(args):
                                  "step streams from HBM, no flush needed",
                            "parallelism": f"replicas x{ws}"},
                 "roofline": roof, "clocks": clk,
-                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": QUERIES_PER_STEP * 32,
-                        "d2h_bytes_per_step": QUERIES_PER_STEP * (8 + 8 * K)},
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": QUERIES_PER_STEP * 24,
+                        "d2h_bytes_per_step": QUERIES_PER_STEP * (4 + 8 * K) + 4},
                 "gpu_launches": args.steps * QUERIES_PER_STEP}
         if not args.no_cpu_baseline and ws == 1:
             line["cpu_baseline"] = cpu_oracle_throughput(4_000_000, 8, "")
@@ -323,6 +346,90 @@ def run_gb300(args):
     fps.fps_release(lib)
     if ws > 1:
         dist.destroy_process_group()
+
+
+def run_latency(args):
+    """Single query over a 1,000,000-record library (24 MB, inside the 129 MB L2): warm latency (library
+    cached in L2 by the previous query), cold latency (a 512 MB scratch buffer written before each query
+    evicts it), and end-to-end latency through the C ABI with host buffers."""
+    import torch
+
+    import paper_1906_06170_gb300 as fps
+    import synth
+
+    torch.cuda.set_device(0)
+    n = args.n if args.n != PAPER_N else 1_000_000
+    lib = fps.fps_library_load(packed=synth.packed(n, 0))
+    info = fps.fps_library_info_get(lib)
+    q = synth.packed(1, synth.query_seed(0))
+    qd = torch.from_numpy(q.view(np.int64).copy()).cuda()
+    oi = torch.empty(K, dtype=torch.int32, device="cuda")
+    od = torch.empty_like(oi)
+    oc = torch.empty(1, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    scratch = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+
+    def one():
+        fps.fps_search_packed(lib, qd[0], K, out_index=oi, out_dist=od, out_count=oc, stream=stream)
+
+    def timed(cold, reps):
+        ts = []
+        for i in range(reps):
+            if cold:
+                scratch.fill_(i & 0xFF)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            one()
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b) * 1e3)
+        return np.array(ts)
+
+    for _ in range(max(args.warmup, 3)):
+        one()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    reps = max(args.steps, 20)
+    warm = timed(False, reps)
+    cold = timed(True, max(reps // 4, 10))
+    clk = clocks.stop()
+    qh = q[0].copy()
+    e2e = []
+    for _ in range(max(reps // 4, 10)):
+        t0 = time.perf_counter()
+        res_i, res_d = fps.fps_search_packed(lib, qh, K)
+        e2e.append((time.perf_counter() - t0) * 1e6)
+    e2e = np.array(e2e)
+    assert len(res_i) == min(K, n) and np.all(np.diff(res_d) >= 0), "latency results malformed"
+    # algorithmic bytes of the bucketed scan (records in buckets within the k-th distance of the query)
+    bc = info["bucket_count"]
+    pq = int(np.unpackbits(q.view(np.uint8), bitorder="little")[:166].sum())
+    tk = int(res_d[-1])
+    alg = 24.0 * bc[max(0, pq - tk): min(166, pq + tk) + 1].sum() + 8.0 * K
+    peak, peak_kind = measured_peak_gbs()
+    p50w, p50c = float(np.median(warm)), float(np.median(cold))
+    line = {"metric": METRIC, "value": n / (p50w * 1e-6) / 1e9, "unit": UNIT, "n_gpus": 1, "steps": reps,
+            "warmup": max(args.warmup, 3), "ms_per_step": p50w / 1e3, "higher_is_better": True,
+            "dtype": "u64", "data": "synthetic",
+            "latency_us": {"warm_p50": p50w, "warm_p99": float(np.percentile(warm, 99)),
+                           "cold_p50": p50c, "cold_p99": float(np.percentile(cold, 99)),
+                           "e2e_host_p50": float(np.median(e2e)), "e2e_host_p99": float(np.percentile(e2e, 99))},
+            "cold_value": n / (p50c * 1e-6) / 1e9,
+            "roofline_cold": {"bound": "hbm", "achieved": alg / (p50c * 1e-6) / 1e9, "peak": peak, "unit": "GB/s",
+                              "frac": alg / (p50c * 1e-6) / 1e9 / peak, "algorithmic_bytes_per_launch": alg,
+                              "note": "a 24 MB launch is dominated by its fixed start and merge time"},
+            "config": {"workload": f"{n:,} generated records (seed 0, 1% planted near-duplicates), 1 query "
+                                   f"(seed 1000), k={K}; warm = library in L2 from the previous query, cold = "
+                                   f"512 MB written before each query", "n_records": n, "k": K,
+                       "peak_source": peak_kind},
+            "clocks": clk,
+            "e2e": {"value": n / (float(np.median(e2e)) * 1e-6) / 1e9, "unit": UNIT, "h2d_bytes_per_step": 32,
+                    "d2h_bytes_per_step": 8 + 8 * K},
+            "gpu_launches": 1}
+    print(json.dumps(line), flush=True)
+    fps.fps_release(lib)
 
 
 def run_batch(args):
@@ -369,6 +476,22 @@ def run_batch(args):
     cnt = oc.cpu().numpy()
     assert np.all(cnt == np.minimum(ks, n)), "batch results malformed"
     value = Q * n / (ms / 1e3) / 1e9
+    # end to end through a captured batch plan (CUDA graph): host queries in, host results out
+    e2e = None
+    if args.path in ("tc_fp8", "popc_batch"):
+        plan = fps.fps_batch_plan_create(lib, ks, path=paths[args.path])
+        for _ in range(2):
+            fps.fps_batch_plan_run(plan, qs)
+        t_e = time.perf_counter()
+        e2e_steps = max(2, min(args.steps, 5))
+        for _ in range(e2e_steps):
+            res = fps.fps_batch_plan_run(plan, qs)
+        e2e_s = (time.perf_counter() - t_e) / e2e_steps
+        assert all(len(r[0]) == min(int(kk), n) for r, kk in zip(res, ks)), "plan results malformed"
+        fps.fps_batch_plan_release(plan)
+        e2e = {"value": Q * n / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": Q * 24,
+               "d2h_bytes_per_step": int(np.sum(ks)) * 8 + Q * 4, "ms_per_step": e2e_s * 1e3,
+               "via": "fps_batch_plan_run (captured graph, host buffers)"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "queries_per_s": Q / (ms / 1e3), "dtype": "u64" if args.path.startswith("popc") else args.path,
@@ -376,7 +499,10 @@ def run_batch(args):
             "config": {"workload": f"{n:,} generated records (seed 0), {Q} queries (seed 1002) with k from "
                                    f"{{1,10,30,100,1000}} per batched call, path {args.path}",
                        "n_records": n, "queries": Q},
-            "clocks": clk}
+            "clocks": clk,
+            "gpu_launches": args.steps * (4 if args.path.startswith("tc") else 3)}
+    if e2e is not None:
+        line["e2e"] = e2e
     print(json.dumps(line), flush=True)
     fps.fps_release(lib)
 
@@ -410,12 +536,16 @@ def run_learned(args):
                        quantile=0.9)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
+    # the non-learned comparison: a per-popcount quantile table fitted on the same labels
+    table = learn.popc_quantile_table(qtr, ttr, 0.9)
     del qtr, ttr
 
     n = args.n
     lib = fps.fps_library_load(packed=synth.packed(n, 0), flags=fps.FPS_LOAD_TC_OPERAND)
     qcal = torch.from_numpy(synth.packed(4096, 999).view(np.int64).copy()).cuda()
-    offset = learn.calibrate_offset(model, qcal, learn.exact_kth(lib, qcal, k), max_fallback=0.0025)
+    tcal = learn.exact_kth(lib, qcal, k)
+    offset = learn.calibrate_offset(model, qcal, tcal, max_fallback=0.0025)
+    t_offset = learn.offset_for(learn.table_tau(table, qcal), tcal.cpu().numpy(), max_fallback=0.0025)
     qs = synth.packed(Q, synth.query_seed(3))
     qd = torch.from_numpy(qs.view(np.int64).copy()).cuda()
     ks = np.full(Q, k, np.int32)
@@ -457,6 +587,15 @@ def run_learned(args):
 
     ms_p = timed(pilot_step, max(2, args.steps // 2), 1)
     assert torch.equal(res_l[0], oi) and torch.equal(res_l[1], od), "learned and sampled-bound results differ"
+    st_t = fps.fps_search_stats()
+    tau_t = torch.from_numpy(learn.table_tau(table, qs, t_offset)).cuda()
+
+    def table_step():
+        fps.fps_search_batch(lib, qd, ks, path=fps.FPS_PATH_LEARNED, tau=tau_t, out_index=oi, out_dist=od,
+                             out_count=oc, offsets=off, stream=stream, stats=st_t)
+
+    ms_t = timed(table_step, max(2, args.steps // 2), 1)
+    assert torch.equal(res_l[0], oi) and torch.equal(res_l[1], od), "learned and table-bound results differ"
     value = Q * n / (ms_l / 1e3) / 1e9
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_l, "higher_is_better": True, "scaling": "weak",
@@ -466,6 +605,11 @@ def run_learned(args):
             "calibration_offset": offset, "train_loss_per_epoch": hist,
             "sampled_bound_tc": {"ms_per_step": ms_p, "queries_per_s": Q / (ms_p / 1e3),
                                  "value": Q * n / (ms_p / 1e3) / 1e9},
+            "popc_table_bound": {"ms_per_step": ms_t, "queries_per_s": Q / (ms_t / 1e3),
+                                 "value": Q * n / (ms_t / 1e3) / 1e9, "candidates": int(st_t.candidates),
+                                 "fallbacks": int(st_t.fallbacks), "fallback_rate": st_t.fallbacks / Q,
+                                 "calibration_offset": t_offset,
+                                 "predictor": "0.9-quantile of the training labels per query popcount"},
             "setup_s": {"labels": round(t_labels, 1), "train": round(t_train, 1)},
             "config": {"workload": f"learned threshold: MLP 167-256-256-1 trained on {4 * per_lib:,} (query, 30th "
                                    f"distance) pairs from 4 x {n_train_lib:,}-record libraries (seeds 1-4); search "
@@ -518,9 +662,24 @@ def run_serve(args):
     sizes_seen = np.array(srv.batch_sizes)
     n_plain = min(nreq, int(os.environ.get("FPS_SERVE_PLAIN_REQUESTS", 4000)))
     plain = serve.latency_stats(srv.run(requests()[:n_plain], batched=False, keep_results=False))
+    # stress: each request carries U{1..512} queries (same arrivals process), far above capacity, so the
+    # served rate is the saturation throughput of the batched back end
+    n_stress = int(os.environ.get("FPS_SERVE_STRESS_REQUESTS", 1500))
+    m = np.array([1 + synth.draw(7, i, 1) % 512 for i in range(n_stress)], np.int64)
+    qstress = synth.packed(int(m.sum()), 1005)
+    starts = np.concatenate([[0], np.cumsum(m)[:-1]])
+    arr_s = serve.poisson_arrivals(n_stress, rate, seed=7)
+    sreqs = [serve.Request(float(t), names[synth.draw(7, i, 2) % 3], qstress[starts[i]: starts[i] + m[i]],
+                           [10, 30, 100][synth.draw(7, i, 3) % 3]) for i, t in enumerate(arr_s)]
+    sdone = srv.run(sreqs, keep_results=False)
+    stress = serve.latency_stats(sdone)
+    comps = sum(r.nq * sizes[r.lib][0] for r in sdone)
+    stress["g_comparisons_per_s"] = comps / stress["span_s"] / 1e9
     line = {"metric": "serving: requests/s and latency, exact top-k", "value": batched["throughput_rps"],
             "unit": "requests/s", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
             "batched": batched, "plain_per_query": plain,
+            "stress_multi_query": dict(stress, note=f"{n_stress} requests of U{{1..512}} queries each "
+                                                    f"({int(m.sum()):,} queries), same arrival rate: saturation"),
             "batch_size": {"mean": float(sizes_seen.mean()), "max": int(sizes_seen.max()), "calls": int(sizes_seen.size)},
             "budget_refusal_ok": refused, "device_bytes_resident": need,
             "config": {"workload": f"Poisson arrivals at {rate:g} req/s, {nreq} requests, k from {{10,30,100}}, "
@@ -537,6 +696,8 @@ def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "latency":
+        run_latency(args)
     elif args.workload == "batch":
         run_batch(args)
     elif args.workload == "learned":

@@ -381,7 +381,7 @@ fps_status get_workspace(Library* L, cudaStream_t s, Workspace** out) {
   w->cand_cap = scan_cand_capacity(L->num_sms);
   size_t st_bytes = (sizeof(ScanState) + 255) / 256 * 256;
   size_t io_bytes = (sizeof(HostIO) + 255) / 256 * 256;
-  size_t bytes = st_bytes + io_bytes + w->cand_cap * sizeof(unsigned long long);
+  size_t bytes = 2 * st_bytes + io_bytes + 2 * w->cand_cap * sizeof(unsigned long long);
   if (cudaMalloc(&w->block, bytes) != cudaSuccess || cudaMallocHost(&w->io_host, sizeof(HostIO)) != cudaSuccess) {
     cudaGetLastError();
     if (w->block) cudaFree(w->block);
@@ -392,7 +392,10 @@ fps_status get_workspace(Library* L, cudaStream_t s, Workspace** out) {
   w->st = reinterpret_cast<ScanState*>(b);
   w->io = reinterpret_cast<HostIO*>(b + st_bytes);
   w->cand = reinterpret_cast<unsigned long long*>(b + st_bytes + io_bytes);
-  if (cudaMemsetAsync(w->io, 0, sizeof(HostIO), s) != cudaSuccess || scan_state_init(w->st, s) != cudaSuccess) {
+  w->st2 = reinterpret_cast<ScanState*>(b + st_bytes + io_bytes + w->cand_cap * sizeof(unsigned long long));
+  w->cand2 = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(w->st2) + st_bytes);
+  if (cudaMemsetAsync(w->io, 0, sizeof(HostIO), s) != cudaSuccess || scan_state_init(w->st, s) != cudaSuccess ||
+      scan_state_init(w->st2, s) != cudaSuccess) {
     cudaGetLastError();
     cudaFree(w->block);
     cudaFreeHost(w->io_host);
@@ -421,7 +424,7 @@ fps_status take_device_error(Workspace* w, cudaStream_t s) {
   if (!e) return FPS_OK;
   // a failed scan may leave its state dirty: clear error word and scan state
   if (cudaMemsetAsync(&w->io->err, 0, sizeof(uint32_t), s) != cudaSuccess || scan_state_init(w->st, s) != cudaSuccess ||
-      cudaStreamSynchronize(s) != cudaSuccess) {
+      scan_state_init(w->st2, s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
     cudaGetLastError();
     return FPS_ERR_CUDA;
   }
@@ -498,22 +501,34 @@ fps_status batch_staging(Workspace* w, size_t dev_bytes, size_t host_bytes) {
   return FPS_OK;
 }
 
-// Queries one after another through the single-query kernel (FPS_PATH_POPC).
+// Queries one after another through the single-query kernel (FPS_PATH_POPC); every
+// search still streams the whole (unpruned) library.  All queries are in device memory
+// before the first launch, so the launches after the first are programmatic dependents of
+// their predecessor: search i+1 streams on the SMs that search i has released while
+// search i merges.  Consecutive searches alternate between the workspace's two scan
+// states; search i+2 reuses search i's state and can only start once search i+1's merge
+// has waited for search i to finish, so a state is never shared by running grids.
 fps_status batch_sequential(Library* L, Workspace* w, const uint64_t* dq, int Q, const int32_t* k, const int64_t* off,
                             int32_t* di, int32_t* dd, int32_t* dc, double tmo, cudaStream_t s) {
-  for (int q = 0; q < Q; ++q) {
+  for (int q = 0; q < Q; ++q) {   // empty results first, so the scan launches stay adjacent
     if (k[q] == 0 || L->n == 0) {
       if (cudaMemsetAsync(dc + q, 0, sizeof(int32_t), s) != cudaSuccess) {
         cudaGetLastError();
         return FPS_ERR_CUDA;
       }
-      continue;
     }
-    if (launch_scan_single(L->dev, dq + 3 * q, k[q], w->st, w->cand, di + off[q], dd + off[q], dc + q, &w->io->err,
-                           L->num_sms, tmo, s) != cudaSuccess) {
+  }
+  int launched = 0;
+  for (int q = 0; q < Q; ++q) {
+    if (k[q] == 0 || L->n == 0) continue;
+    ScanState* st = (launched & 1) ? w->st2 : w->st;
+    unsigned long long* cand = (launched & 1) ? w->cand2 : w->cand;
+    if (launch_scan_single(L->dev, dq + 3 * q, k[q], st, cand, di + off[q], dd + off[q], dc + q, &w->io->err,
+                           L->num_sms, tmo, s, launched > 0) != cudaSuccess) {
       cudaGetLastError();
       return FPS_ERR_CUDA;
     }
+    ++launched;
   }
   return FPS_OK;
 }

@@ -73,6 +73,9 @@ struct Workspace {
   HostIO* io = nullptr;          // device
   HostIO* io_host = nullptr;     // pinned host
   unsigned long long* cand = nullptr;
+  // second scan state and candidate array: consecutive searches of one sequence alternate
+  ScanState* st2 = nullptr;
+  unsigned long long* cand2 = nullptr;
   size_t cand_cap = 0;
   void* block = nullptr;         // the one device allocation holding st, io and cand
   // batched-path scratch (grown on demand)
@@ -149,8 +152,12 @@ struct ScanConfig {
 ScanConfig scan_config_for(int k);
 size_t scan_cand_capacity(int num_sms);  // keys needed by the largest configuration
 cudaError_t scan_state_init(ScanState* st, cudaStream_t s);
+// programmatic: launch as a programmatic dependent of the previous kernel on s, which must be
+// a scan of the same sequence using the other scan state (and the other candidate array); the
+// grid then streams while that scan merges (see batch_sequential).
 cudaError_t launch_scan_single(const DevLib& lib, const uint64_t* d_query, int k, ScanState* st,
                                unsigned long long* cand, int32_t* out_idx, int32_t* out_dist, int32_t* out_count,
-                               uint32_t* err, int num_sms, double timeout_s, cudaStream_t s);
+                               uint32_t* err, int num_sms, double timeout_s, cudaStream_t s,
+                               bool programmatic = false);
 
 }  // namespace fps

@@ -624,6 +624,13 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
   __syncthreads();
   if (!tb.is_last) return;
   __threadfence();
+  // In a sequence of searches (programmatic dependent launches, alternating
+  // between two scan states) this grid may have started while the previous
+  // search was still merging.  The merge waits for that grid to finish, then
+  // lets the next search start on the SMs this grid has already released.
+  // Without a programmatic dependency both instructions return at once.
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 
   unsigned long long* fin = reinterpret_cast<unsigned long long*>(smem);
   unsigned long long* ties = fin + kFinCap;
@@ -777,7 +784,7 @@ __global__ void scan_state_init_kernel(ScanState* st) {
 template <int WARPS, int CAP>
 cudaError_t launch_cfg(const DevLib& lib, const uint64_t* q, int k, ScanState* st, unsigned long long* cand,
                        int32_t* oi, int32_t* od, int32_t* oc, uint32_t* err, int num_sms, uint64_t tns,
-                       cudaStream_t s) {
+                       bool programmatic, cudaStream_t s) {
   using L = Smem<WARPS, CAP>;
   auto kern = scan_single_kernel<WARPS, CAP>;
   static bool configured = false;  // attribute set once per process (idempotent)
@@ -786,8 +793,17 @@ cudaError_t launch_cfg(const DevLib& lib, const uint64_t* q, int k, ScanState* s
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  kern<<<num_sms, WARPS * 32, L::total, s>>>(lib, q, k, st, cand, oi, od, oc, err, tns);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(static_cast<unsigned>(num_sms));
+  cfg.blockDim = dim3(WARPS * 32);
+  cfg.dynamicSmemBytes = L::total;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = programmatic ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, lib, q, k, st, cand, oi, od, oc, err, tns);
 }
 
 constexpr int kSmallWarps = 16, kSmallCap = 256;   // k <= 128
@@ -814,13 +830,13 @@ cudaError_t scan_state_init(ScanState* st, cudaStream_t s) {
 
 cudaError_t launch_scan_single(const DevLib& lib, const uint64_t* d_query, int k, ScanState* st,
                                unsigned long long* cand, int32_t* out_idx, int32_t* out_dist, int32_t* out_count,
-                               uint32_t* err, int num_sms, double timeout_s, cudaStream_t s) {
+                               uint32_t* err, int num_sms, double timeout_s, cudaStream_t s, bool programmatic) {
   uint64_t tns = static_cast<uint64_t>((timeout_s > 0 ? timeout_s : 2.0) * 1e9);
   if (k <= kSmallCap - kTile)
     return launch_cfg<kSmallWarps, kSmallCap>(lib, d_query, k, st, cand, out_idx, out_dist, out_count, err, num_sms,
-                                              tns, s);
+                                              tns, programmatic, s);
   return launch_cfg<kLargeWarps, kLargeCap>(lib, d_query, k, st, cand, out_idx, out_dist, out_count, err, num_sms,
-                                            tns, s);
+                                            tns, programmatic, s);
 }
 
 }  // namespace fps
@@ -924,7 +940,7 @@ extern "C" fps_status fps_search_noalloc(fps_library lib, const uint64_t* query,
     noalloc_prepare_kernel<<<1, 192, 0, s>>>(st, err);
     if (cudaGetLastError() != cudaSuccess ||
         launch_cfg<kSmallWarps, kSmallCap>(L->dev, query, k, st, cand, out_index, out_dist, out_count, err,
-                                           L->num_sms, 2000000000ull, s) != cudaSuccess) {
+                                           L->num_sms, 2000000000ull, false, s) != cudaSuccess) {
       status = FPS_ERR_CUDA;
     } else {
       noalloc_finish_kernel<<<1, 32, 0, s>>>(err, out_count);

@@ -72,14 +72,50 @@ def train(model, queries, targets, epochs: int = 8, batch: int = 4096, lr: float
     return history
 
 
-def calibrate_offset(model, queries, targets, max_fallback: float = 0.002) -> float:
-    """Smallest integer offset delta with P(ceil(pred + delta) < target) <= max_fallback on held-out queries."""
-    pred = fps_mlp_predict(model, queries).float().cpu().numpy()[: int(queries.shape[0])]
-    t = targets.float().cpu().numpy()
+def offset_for(pred, targets, max_fallback: float = 0.002) -> float:
+    """Smallest integer offset delta with P(ceil(pred + delta) < target) <= max_fallback."""
+    pred = np.asarray(pred, np.float64)
+    t = np.asarray(targets, np.float64)
     for delta in range(-8, 40):
         if np.mean(np.ceil(pred + delta) < t) <= max_fallback:
             return float(delta)
     return 40.0
+
+
+def calibrate_offset(model, queries, targets, max_fallback: float = 0.002) -> float:
+    """offset_for() of the model's predictions on held-out queries (CUDA tensors)."""
+    pred = fps_mlp_predict(model, queries).float().cpu().numpy()[: int(queries.shape[0])]
+    return offset_for(pred, targets.float().cpu().numpy(), max_fallback)
+
+
+def query_popcounts(queries) -> np.ndarray:
+    """popc of packed queries (host uint64 [Q, 3], or a CUDA int64 tensor)."""
+    if hasattr(queries, "cpu"):
+        queries = queries.cpu().numpy()
+    q = np.ascontiguousarray(np.asarray(queries).view(np.uint64).reshape(-1, 3))
+    return np.unpackbits(q.view(np.uint8), axis=1, bitorder="little")[:, :166].sum(1).astype(np.int64)
+
+
+def popc_quantile_table(queries, targets, quantile: float = 0.9) -> np.ndarray:
+    """Non-learned predictor of the k-th distance: for each query popcount p (0..166), the given quantile
+    of the training targets whose query has popcount p; popcounts with no training query take the
+    value of the nearest popcount that has one."""
+    pc = query_popcounts(queries)
+    t = targets.float().cpu().numpy() if hasattr(targets, "cpu") else np.asarray(targets, np.float64)
+    table = np.full(167, np.nan)
+    for p in np.unique(pc):
+        table[p] = np.quantile(t[pc == p], quantile)
+    have = np.flatnonzero(~np.isnan(table))
+    if have.size == 0:
+        raise ValueError("no training targets")
+    for p in np.flatnonzero(np.isnan(table)):
+        table[p] = table[have[np.argmin(np.abs(have - p))]]
+    return table.astype(np.float32)
+
+
+def table_tau(table, queries, offset: float = 0.0) -> np.ndarray:
+    """Bounds (float32 [Q]) from a popcount table, including an offset."""
+    return (np.asarray(table, np.float32)[query_popcounts(queries)] + np.float32(offset)).astype(np.float32)
 
 
 def predict_tau(model, queries, offset: float = 0.0):
@@ -123,5 +159,5 @@ def load(path: str, device: int = 0):
     return model, meta
 
 
-__all__ = ["exact_kth", "init_params", "train", "calibrate_offset", "predict_tau", "learned_search", "save", "load",
-           "batch_offsets"]
+__all__ = ["exact_kth", "init_params", "train", "offset_for", "calibrate_offset", "predict_tau", "learned_search",
+           "query_popcounts", "popc_quantile_table", "table_tau", "save", "load", "batch_offsets"]

@@ -5,8 +5,10 @@ The paper decouples its web tier from the compute back end with a queue
 to completion (Sec. 4.4).  Here the back end is one process holding several
 libraries in GPU memory; requests arrive over time, wait in one queue per
 library, and are served in dynamic batches (up to max_batch requests of one
-library per call, oldest library first) through fps_search_batch.  The plain
-baseline serves the same arrivals one request at a time with
+library per call, oldest library first) through fps_search_batch.  A request
+carries one query (shape [3]) or several (shape [m, 3], all with the request's
+k); a batch takes whole requests while their queries fit in max_batch.  The
+plain baseline serves the same arrivals one request at a time with
 fps_search_packed.  Latency = completion - arrival, on the host clock.
 
 Only host-side scheduling lives here; every search step runs in the library's
@@ -23,12 +25,17 @@ from . import FPS_PATH_AUTO, FPS_PATH_POPC, FPS_PATH_POPC_BATCH, fps_search_batc
 
 
 class Request:
+    """result: (index, distance) for a one-query request, a list of them for a [m, 3] request."""
     __slots__ = ("arrival", "lib", "query", "k", "done", "result")
 
     def __init__(self, arrival, lib, query, k):
         self.arrival, self.lib, self.query, self.k = arrival, lib, query, k
         self.done = None
         self.result = None
+
+    @property
+    def nq(self) -> int:
+        return 1 if np.ndim(self.query) == 1 else int(np.shape(self.query)[0])
 
 
 def choose_path(q: int, has_tc: bool) -> int:
@@ -56,13 +63,16 @@ class Server:
         self.batch_sizes = []
 
     def _serve_batch(self, name, reqs):
-        qs = np.stack([r.query for r in reqs])
-        ks = np.array([r.k for r in reqs], np.int32)
-        self.batch_sizes.append(len(reqs))
+        qs = np.concatenate([np.reshape(r.query, (-1, 3)) for r in reqs])
+        ks = np.concatenate([np.full(r.nq, r.k, np.int32) for r in reqs])
+        self.batch_sizes.append(len(ks))
         res = self.batch_fn(name, qs, ks)
         now = time.perf_counter()
-        for r, out in zip(reqs, res):
-            r.done, r.result = now, out
+        pos = 0
+        for r in reqs:
+            r.done = now
+            r.result = res[pos] if np.ndim(r.query) == 1 else list(res[pos: pos + r.nq])
+            pos += r.nq
 
     def run(self, requests, batched: bool = True, keep_results: bool = True):
         """Replay requests (sorted by arrival, seconds from start) in real time; returns them completed."""
@@ -87,7 +97,11 @@ class Server:
             name = min(live, key=lambda nm: queues[nm][0].arrival)      # oldest waiting request first
             q = queues[name]
             if batched:
-                batch = [q.popleft() for _ in range(min(self.max_batch, len(q)))]
+                batch, total = [q.popleft()], 0
+                total = batch[0].nq
+                while q and total + q[0].nq <= self.max_batch:
+                    total += q[0].nq
+                    batch.append(q.popleft())
                 self._serve_batch(name, batch)
                 served += len(batch)
             else:
@@ -106,9 +120,11 @@ class Server:
 def latency_stats(reqs):
     lat = np.array([r.done - r.arrival for r in reqs])
     span = max(r.done for r in reqs) - min(r.arrival for r in reqs)
-    return {"requests": len(reqs), "p50_ms": float(np.percentile(lat, 50) * 1e3),
+    nq = sum(r.nq for r in reqs)
+    return {"requests": len(reqs), "queries": nq, "p50_ms": float(np.percentile(lat, 50) * 1e3),
             "p99_ms": float(np.percentile(lat, 99) * 1e3), "mean_ms": float(lat.mean() * 1e3),
-            "throughput_rps": len(reqs) / span if span > 0 else float("nan")}
+            "throughput_rps": len(reqs) / span if span > 0 else float("nan"),
+            "throughput_qps": nq / span if span > 0 else float("nan"), "span_s": span}
 
 
 def poisson_arrivals(n: int, rate: float, seed: int):

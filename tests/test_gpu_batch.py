@@ -97,3 +97,31 @@ def test_batch_workload_one_million_mixed_k(gpu_lib):
         check_batch(fps, lib, text, qs, ks, fps.FPS_PATH_POPC_BATCH)
     finally:
         fps.fps_release(lib)
+
+
+def test_sequential_chain_alternates_states_exactly(gpu_lib):
+    """FPS_PATH_POPC runs the queries one after another, each launch after the first a programmatic
+    dependent of the previous one on the other scan state.  Mixed k switches between the two kernel
+    configurations inside the chain, k = 0 entries are skipped, a run of equal records forces the
+    merge's bisection path mid-chain, and repeated calls plus a single search afterwards reuse both
+    states."""
+    fps = gpu_lib
+    x = qstrs(synth.packed(2, 1040))
+    rows = qstrs(synth.packed(150000, 40)) + [x[0]] * 20000 + qstrs(synth.packed(30001, 41))
+    text = synth.strings_to_text(rows)
+    lib = fps.fps_library_load(text=text)
+    try:
+        qs = np.concatenate([synth.packed(21, 1041), np.stack([fps.fps_pack_query(x[0])] * 3)])
+        cyc = [30, 0, 1, 1920, 100, 129, 10, 1000]
+        ks = np.array([cyc[i % len(cyc)] for i in range(len(qs))], np.int32)
+        want = oracle.topk_many(text, qstrs(qs), ks)
+        for rep in range(2):
+            got = fps.fps_search_batch(lib, qs, ks, path=fps.FPS_PATH_POPC)
+            for q, ((gi, gd), (wi, wd)) in enumerate(zip(got, want)):
+                assert np.array_equal(gi, wi) and np.array_equal(gd, wd), (rep, q, ks[q])
+        check_batch(fps, lib, text, qs, ks, fps.FPS_PATH_POPC, device_io=True)
+        gi, gd = fps.fps_search_packed(lib, qs[3], 50)
+        wi, wd, _ = oracle.topk(text, qstrs(qs[3:4])[0], 50)
+        assert np.array_equal(gi, wi) and np.array_equal(gd, wd)
+    finally:
+        fps.fps_release(lib)

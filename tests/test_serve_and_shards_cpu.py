@@ -67,6 +67,37 @@ def test_serving_loop_schedules_every_request_once(fps):
     assert serve.choose_path(512, False) == fps.FPS_PATH_POPC_BATCH
 
 
+def test_serving_loop_multi_query_requests(fps):
+    """Requests of 1..40 queries: batches hold whole requests up to max_batch queries, and every request gets
+    its own results back in order."""
+    from paper_1906_06170_gb300 import serve
+
+    calls = []
+
+    def batch_fn(name, qs, ks):
+        calls.append(len(ks))
+        return [(np.array([int(qs[i, 0] % 100003)], np.int32), np.array([int(ks[i])], np.int32)) for i in range(len(ks))]
+
+    arr = serve.poisson_arrivals(300, 50000.0, seed=6)
+    rng = np.random.default_rng(7)
+    reqs, base = [], 0
+    for i, t in enumerate(arr):
+        m = int(rng.integers(1, 41))
+        q = synth.packed(m, 2000 + i) if i % 3 else synth.packed(1, 2000 + i)[0]
+        reqs.append(serve.Request(float(t), ["a", "b"][i % 2], q, [10, 30, 100][i % 3]))
+    srv = serve.Server({"a": None, "b": None}, max_batch=64, batch_fn=batch_fn)
+    done = srv.run(reqs)
+    assert sum(calls) == sum(r.nq for r in done) and max(calls) <= 64
+    for r in done:
+        qq = np.reshape(r.query, (-1, 3))
+        got = [r.result] if np.ndim(r.query) == 1 else r.result
+        assert len(got) == r.nq
+        for row, (gi, gd) in zip(qq, got):
+            assert gi[0] == int(row[0] % 100003) and gd[0] == r.k
+    st = serve.latency_stats(done)
+    assert st["queries"] == sum(r.nq for r in done) and st["throughput_qps"] >= st["throughput_rps"]
+
+
 def _free_port():
     s = socket.socket()
     s.bind(("127.0.0.1", 0))

@@ -140,6 +140,7 @@ typedef struct {
   int64_t fallbacks;             /* queries that needed the exact fallback scan */
   int64_t candidates;            /* records accepted under the running bounds (batched paths) */
   int64_t path_used;             /* fps_path actually run */
+  int64_t device_fallbacks;      /* of the fallbacks, those re-run inside a batch plan's graph */
 } fps_search_stats;
 
 typedef struct {
@@ -217,8 +218,12 @@ fps_status fps_search_noalloc(fps_library lib, const uint64_t* query, int k, int
  * host queries (Q x FPS_WORDS) and, when learned, host predictions tau[Q];
  * results go to host arrays laid out by the prefix sums of k (as in
  * fps_search_batch); the call returns when they are written.  Queries that
- * need the exact fallback are re-run after the graph.  A plan must not be run
- * concurrently with itself; it must be released before its library.
+ * need the exact fallback (candidate overflow, or a predicted bound below the
+ * k-th distance) are re-run inside the graph: a conditional WHILE node runs the
+ * single-query scan once per such query, reading the query, k and output
+ * places from a device-side descriptor, so no host round trip is needed.  A
+ * plan must not be run concurrently with itself; it must be released before
+ * its library.
  */
 typedef struct fps_batch_plan_s* fps_batch_plan;
 fps_status fps_batch_plan_create(fps_library lib, int Q, const int32_t* k, int path, int learned, fps_batch_plan* out);

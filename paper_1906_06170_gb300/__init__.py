@@ -52,7 +52,7 @@ class fps_library_info(ctypes.Structure):
 
 class fps_search_stats(ctypes.Structure):
     _fields_ = [("queries", ctypes.c_int64), ("fallbacks", ctypes.c_int64), ("candidates", ctypes.c_int64),
-                ("path_used", ctypes.c_int64)]
+                ("path_used", ctypes.c_int64), ("device_fallbacks", ctypes.c_int64)]
 
 
 class fps_search_opts(ctypes.Structure):

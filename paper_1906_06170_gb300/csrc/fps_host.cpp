@@ -469,6 +469,7 @@ fps_status search_one_host(Library* L, const uint64_t q[3], int k, int32_t* out_
   if (opts && opts->stats) {
     opts->stats->queries = 1;
     opts->stats->fallbacks = 0;
+    opts->stats->device_fallbacks = 0;
     opts->stats->candidates = 0;
     opts->stats->path_used = FPS_PATH_POPC;
   }
@@ -776,6 +777,7 @@ fps_status search_batch_impl(Library* L, const uint64_t* queries, int Q, const i
       if (opts && opts->stats) {
         opts->stats->queries = Q;
         opts->stats->fallbacks = nf;
+        opts->stats->device_fallbacks = 0;
         opts->stats->path_used = tau ? FPS_PATH_LEARNED : FPS_PATH_TC_FP8;
       }
       return FPS_OK;
@@ -794,6 +796,7 @@ fps_status search_batch_impl(Library* L, const uint64_t* queries, int Q, const i
     if (st == FPS_OK && opts && opts->stats) {
       opts->stats->queries = Q;
       opts->stats->fallbacks = nf;
+      opts->stats->device_fallbacks = 0;
       opts->stats->path_used = tau ? FPS_PATH_LEARNED : path;
     }
     return st;
@@ -838,6 +841,7 @@ fps_status search_batch_impl(Library* L, const uint64_t* queries, int Q, const i
   if (opts && opts->stats) {
     opts->stats->queries = Q;
     opts->stats->fallbacks = 0;
+    opts->stats->device_fallbacks = 0;
     opts->stats->candidates = 0;
     opts->stats->path_used = FPS_PATH_POPC;
   }
@@ -859,8 +863,15 @@ struct BatchPlan {
   uint32_t* err = nullptr;   // device error word
   uint32_t* err_host = nullptr;
   cudaStream_t cap = nullptr;
+  cudaStream_t cap_body = nullptr;   // captures the fallback loop's body
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  // device-side exact fallback: its own scan state, candidate keys and search slot
+  char* fb = nullptr;
+  ScanState* fb_st = nullptr;
+  ScanSlot* fb_slot = nullptr;
+  unsigned long long* fb_cand = nullptr;
+  uint32_t* fb_count_host = nullptr;  // queries the graph re-ran (pinned)
 };
 
 void free_plan(BatchPlan* P) {
@@ -869,6 +880,9 @@ void free_plan(BatchPlan* P) {
   if (P->exec) cudaGraphExecDestroy(P->exec);
   if (P->graph) cudaGraphDestroy(P->graph);
   if (P->cap) cudaStreamDestroy(P->cap);
+  if (P->cap_body) cudaStreamDestroy(P->cap_body);
+  if (P->fb) cudaFree(P->fb);
+  if (P->fb_count_host) cudaFreeHost(P->fb_count_host);
   if (P->db) cudaFree(P->db);
   if (P->hb) cudaFreeHost(P->hb);
   if (P->err) cudaFree(P->err);
@@ -876,16 +890,64 @@ void free_plan(BatchPlan* P) {
   delete P;
 }
 
-// Enqueue the whole batch on stream s (used once eagerly, then under capture).
-cudaError_t plan_enqueue(BatchPlan* P, double tmo, cudaStream_t s) {
+// The exact fallback inside the graph: a first pick, then a WHILE node whose body scans the
+// picked query (indirect launch of the single-query scan) and picks the next one, until no
+// query with count -2 is left.  Captured on s (being captured); the body on P->cap_body.
+cudaError_t plan_capture_fallback(BatchPlan* P, double tmo, cudaStream_t s) {
+  const uint64_t* dq = reinterpret_cast<const uint64_t*>(P->db + P->lay.d_q);
+  const int32_t* dk = reinterpret_cast<const int32_t*>(P->db + P->lay.d_k);
+  const int64_t* doo = reinterpret_cast<const int64_t*>(P->db + P->lay.d_oo);
+  int32_t* di = reinterpret_cast<int32_t*>(P->db + P->lay.d_oi);
+  int32_t* dd = reinterpret_cast<int32_t*>(P->db + P->lay.d_od);
+  int32_t* dc = reinterpret_cast<int32_t*>(P->db + P->lay.d_oc);
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &g);
+  if (e != cudaSuccess) return e;
+  if (cs != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureInvalidated;
+  cudaGraphConditionalHandle h;
+  e = cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault);
+  if (e == cudaSuccess) e = launch_fallback_pick(dq, dk, doo, di, dd, dc, P->Q, P->fb_slot, true, h, s);
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  if (e == cudaSuccess) e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd);
+  if (e != cudaSuccess) return e;
+  cudaGraphNodeParams np = {};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t loop = nullptr;
+  e = cudaGraphAddNode(&loop, g, deps, nullptr, nd, &np);
+  if (e != cudaSuccess) return e;
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  e = cudaStreamBeginCaptureToGraph(P->cap_body, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  cudaError_t e2 = launch_scan_indirect(P->L->dev, P->fb_slot, P->fb_st, P->fb_cand, P->err, P->L->num_sms, tmo,
+                                        P->cap_body);
+  if (e2 == cudaSuccess) e2 = launch_fallback_pick(dq, dk, doo, di, dd, dc, P->Q, P->fb_slot, false, h, P->cap_body);
+  cudaGraph_t captured = nullptr;
+  e = cudaStreamEndCapture(P->cap_body, &captured);
+  if (e2 != cudaSuccess) return e2;
+  if (e != cudaSuccess) return e;
+  return cudaStreamUpdateCaptureDependencies(s, &loop, nullptr, 1, cudaStreamSetCaptureDependencies);
+}
+
+// Enqueue the whole batch on stream s (once eagerly, then under capture).  The device-side
+// fallback needs a graph (its loop is a conditional node), so only the captured run has it;
+// the eager run's results are discarded.
+cudaError_t plan_enqueue(BatchPlan* P, double tmo, cudaStream_t s, bool captured) {
   const BatchDev b = batch_dev(P->db, P->lay, P->Q, nullptr, nullptr, nullptr, P->err);
   const float* tau_dev = P->learned ? reinterpret_cast<const float*>(P->db + P->lay.d_tau) : nullptr;
   cudaError_t e = cudaMemcpyAsync(P->db, P->hb, P->lay.plan_end, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = enqueue_batch(P->L, b, P->db, P->lay, P->tc, tau_dev, tmo, s);
+  if (e == cudaSuccess && captured) e = plan_capture_fallback(P, tmo, s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(P->hb + P->lay.out_begin, P->db + P->lay.out_begin, P->lay.out_end - P->lay.out_begin,
                         cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(P->err_host, P->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && captured)
+    e = cudaMemcpyAsync(P->fb_count_host, &P->fb_slot->nfallback, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
   return e;
 }
 
@@ -1152,20 +1214,44 @@ fps_status fps_batch_plan_create(fps_library lib, int Q, const int32_t* k, int p
   if (!g.ok || cudaMalloc(&P->db, P->lay.bytes) != cudaSuccess || cudaMallocHost(&P->hb, hbytes) != cudaSuccess ||
       cudaMalloc(&P->err, 256) != cudaSuccess || cudaMallocHost(&P->err_host, sizeof(uint32_t)) != cudaSuccess ||
       cudaMemset(P->err, 0, 256) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&P->cap, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaStreamCreateWithFlags(&P->cap, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&P->cap_body, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
     free_plan(P);
     return FPS_ERR_CUDA;
   }
+  {
+    // the fallback's scan state, slot and candidate keys
+    const size_t st_bytes = (sizeof(ScanState) + 255) / 256 * 256;
+    const size_t slot_bytes = (sizeof(ScanSlot) + 255) / 256 * 256;
+    const size_t cand_bytes = scan_cand_capacity(L->num_sms) * sizeof(unsigned long long);
+    if (cudaMalloc(&P->fb, st_bytes + slot_bytes + cand_bytes) != cudaSuccess ||
+        cudaMallocHost(&P->fb_count_host, sizeof(uint32_t)) != cudaSuccess) {
+      cudaGetLastError();
+      free_plan(P);
+      return FPS_ERR_CUDA;
+    }
+    P->fb_st = reinterpret_cast<ScanState*>(P->fb);
+    P->fb_slot = reinterpret_cast<ScanSlot*>(P->fb + st_bytes);
+    P->fb_cand = reinterpret_cast<unsigned long long*>(P->fb + st_bytes + slot_bytes);
+    *P->fb_count_host = 0;
+    if (scan_state_init(P->fb_st, P->cap) != cudaSuccess ||
+        cudaMemsetAsync(P->fb_slot, 0, sizeof(ScanSlot), P->cap) != cudaSuccess ||
+        scan_indirect_prepare() != cudaSuccess) {
+      cudaGetLastError();
+      free_plan(P);
+      return FPS_ERR_CUDA;
+    }
+  }
   std::memset(P->hb, 0, hbytes);
   fill_plan(P->hb, P->lay, nullptr, Q, P->k.data(), P->coff, P->off.data(), nullptr, true);
   // one eager run (sets kernel attributes, checks the sequence), then capture the same sequence
-  cudaError_t e = plan_enqueue(P, 2.0, P->cap);
+  cudaError_t e = plan_enqueue(P, 2.0, P->cap, false);
   if (e == cudaSuccess) e = cudaStreamSynchronize(P->cap);
   if (e == cudaSuccess) e = cudaMemset(P->err, 0, 256);
   if (e == cudaSuccess) e = cudaStreamBeginCapture(P->cap, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
-    cudaError_t e2 = plan_enqueue(P, 2.0, P->cap);
+    cudaError_t e2 = plan_enqueue(P, 2.0, P->cap, true);
     e = cudaStreamEndCapture(P->cap, &P->graph);
     if (e2 != cudaSuccess) e = e2;
   }
@@ -1210,7 +1296,8 @@ fps_status fps_batch_plan_run(fps_batch_plan plan, const uint64_t* queries, cons
                     out_count, &o, false, s, &nf);
   if (st == FPS_OK && stats) {
     stats->queries = P->Q;
-    stats->fallbacks = nf;
+    stats->fallbacks = nf + *P->fb_count_host;
+    stats->device_fallbacks = *P->fb_count_host;
     stats->path_used = P->learned ? FPS_PATH_LEARNED : (P->tc ? FPS_PATH_TC_FP8 : FPS_PATH_POPC_BATCH);
   }
   return st;

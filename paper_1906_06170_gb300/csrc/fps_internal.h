@@ -141,6 +141,20 @@ cudaError_t tc_pack_queries(const uint64_t* q, int Q, uint8_t* op, cudaStream_t 
 cudaError_t tc_scan(const DevLib& lib, const BatchDev& b, const uint8_t* lib_op, const uint8_t* q_op, int num_sms,
                     double timeout_s, cudaStream_t s);
 
+// Description of one search for the indirect scan launch (device memory).  The device-side
+// fallback of a captured batch fills it for each query it re-runs; cursor and nfallback are
+// that loop's position and count.
+struct ScanSlot {
+  const uint64_t* query;
+  int32_t* out_idx;
+  int32_t* out_dist;
+  int32_t* out_count;
+  int32_t k;
+  int32_t cursor;
+  uint32_t nfallback;
+  uint32_t pad;
+};
+
 // ---- kernels (fps_scan.cu)
 // Scan configuration chosen for a given k.
 struct ScanConfig {
@@ -159,5 +173,15 @@ cudaError_t launch_scan_single(const DevLib& lib, const uint64_t* d_query, int k
                                unsigned long long* cand, int32_t* out_idx, int32_t* out_dist, int32_t* out_count,
                                uint32_t* err, int num_sms, double timeout_s, cudaStream_t s,
                                bool programmatic = false);
+// The search a ScanSlot describes (k <= FPS_K_MAX); call scan_indirect_prepare once before
+// capturing such a launch into a graph.
+cudaError_t scan_indirect_prepare();
+cudaError_t launch_scan_indirect(const DevLib& lib, const ScanSlot* slot, ScanState* st, unsigned long long* cand,
+                                 uint32_t* err, int num_sms, double timeout_s, cudaStream_t s);
+// Captured into a graph only: picks the next query with count -2 into the slot and sets the
+// WHILE node's condition h (first = start from query 0 and reset the count).
+cudaError_t launch_fallback_pick(const uint64_t* queries, const int32_t* k, const int64_t* out_off, int32_t* oi,
+                                 int32_t* od, int32_t* oc, int Q, ScanSlot* slot, bool first,
+                                 cudaGraphConditionalHandle h, cudaStream_t s);
 
 }  // namespace fps

@@ -333,10 +333,16 @@ struct Smem {
 // ---------------------------------------------------------------------- kernel
 template <int WARPS, int CAP>
 __global__ void __launch_bounds__(WARPS * 32, 1)
-    scan_single_kernel(DevLib lib, const uint64_t* __restrict__ query, int k, ScanState* st,
-                       unsigned long long* __restrict__ cand, int32_t* __restrict__ out_idx,
-                       int32_t* __restrict__ out_dist, int32_t* __restrict__ out_count, uint32_t* err,
-                       uint64_t timeout_ns) {
+    scan_single_kernel(DevLib lib, const uint64_t* query_arg, int k_arg, ScanState* st,
+                       unsigned long long* __restrict__ cand, int32_t* out_idx_arg, int32_t* out_dist_arg,
+                       int32_t* out_count_arg, uint32_t* err, uint64_t timeout_ns, const ScanSlot* slot) {
+  // indirect launch (the device-side fallback of a captured batch): the search is
+  // described by a slot that a preceding kernel of the graph filled
+  const uint64_t* __restrict__ query = slot ? slot->query : query_arg;
+  const int k = slot ? slot->k : k_arg;
+  int32_t* __restrict__ out_idx = slot ? slot->out_idx : out_idx_arg;
+  int32_t* __restrict__ out_dist = slot ? slot->out_dist : out_dist_arg;
+  int32_t* __restrict__ out_count = slot ? slot->out_count : out_count_arg;
   extern __shared__ __align__(128) unsigned char smem[];
   using L = Smem<WARPS, CAP>;
   unsigned char* ring_all = smem;
@@ -782,17 +788,25 @@ __global__ void scan_state_init_kernel(ScanState* st) {
 }
 
 template <int WARPS, int CAP>
-cudaError_t launch_cfg(const DevLib& lib, const uint64_t* q, int k, ScanState* st, unsigned long long* cand,
-                       int32_t* oi, int32_t* od, int32_t* oc, uint32_t* err, int num_sms, uint64_t tns,
-                       bool programmatic, cudaStream_t s) {
-  using L = Smem<WARPS, CAP>;
-  auto kern = scan_single_kernel<WARPS, CAP>;
+cudaError_t configure_cfg() {
   static bool configured = false;  // attribute set once per process (idempotent)
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(L::total));
+    cudaError_t e = cudaFuncSetAttribute(scan_single_kernel<WARPS, CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(Smem<WARPS, CAP>::total));
     if (e != cudaSuccess) return e;
     configured = true;
   }
+  return cudaSuccess;
+}
+
+template <int WARPS, int CAP>
+cudaError_t launch_cfg(const DevLib& lib, const uint64_t* q, int k, ScanState* st, unsigned long long* cand,
+                       int32_t* oi, int32_t* od, int32_t* oc, uint32_t* err, int num_sms, uint64_t tns,
+                       bool programmatic, cudaStream_t s, const ScanSlot* slot = nullptr) {
+  using L = Smem<WARPS, CAP>;
+  auto kern = scan_single_kernel<WARPS, CAP>;
+  cudaError_t ce = configure_cfg<WARPS, CAP>();
+  if (ce != cudaSuccess) return ce;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(static_cast<unsigned>(num_sms));
   cfg.blockDim = dim3(WARPS * 32);
@@ -803,7 +817,42 @@ cudaError_t launch_cfg(const DevLib& lib, const uint64_t* q, int k, ScanState* s
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = programmatic ? 1 : 0;
-  return cudaLaunchKernelEx(&cfg, kern, lib, q, k, st, cand, oi, od, oc, err, tns);
+  return cudaLaunchKernelEx(&cfg, kern, lib, q, k, st, cand, oi, od, oc, err, tns, slot);
+}
+
+// Device-side fallback of a captured batch: find the next query whose count is -2 (it needs
+// the exact scan), describe it in the slot and set the graph's loop condition (1 = found).
+// One warp; the only caller of cudaGraphSetConditional is lane 0.
+__global__ void fallback_pick_kernel(const uint64_t* queries, const int32_t* k, const int64_t* out_off,
+                                     int32_t* oi, int32_t* od, int32_t* oc, int Q, ScanSlot* slot, int first,
+                                     cudaGraphConditionalHandle h) {
+  const int lane = threadIdx.x;
+  const int from = first ? 0 : slot->cursor + 1;
+  int found = -1;
+  for (int base = from; base < Q; base += 32) {
+    const int q = base + lane;
+    const uint32_t b = __ballot_sync(kFull, q < Q && oc[q] == -2 && k[q] > 0);
+    if (b) {
+      found = base + __ffs(b) - 1;
+      break;
+    }
+  }
+  if (lane == 0) {
+    if (first) slot->nfallback = 0u;
+    if (found >= 0) {
+      slot->query = queries + 3 * static_cast<size_t>(found);
+      slot->k = k[found];
+      slot->out_idx = oi + out_off[found];
+      slot->out_dist = od + out_off[found];
+      slot->out_count = oc + found;
+      slot->cursor = found;
+      slot->nfallback += 1u;
+    } else {
+      slot->k = 0;
+      slot->cursor = Q;
+    }
+    cudaGraphSetConditional(h, found >= 0 ? 1u : 0u);
+  }
 }
 
 constexpr int kSmallWarps = 16, kSmallCap = 256;   // k <= 128
@@ -825,6 +874,23 @@ size_t scan_cand_capacity(int num_sms) {
 
 cudaError_t scan_state_init(ScanState* st, cudaStream_t s) {
   scan_state_init_kernel<<<1, 192, 0, s>>>(st);
+  return cudaGetLastError();
+}
+
+cudaError_t scan_indirect_prepare() { return configure_cfg<kLargeWarps, kLargeCap>(); }
+
+cudaError_t launch_scan_indirect(const DevLib& lib, const ScanSlot* slot, ScanState* st, unsigned long long* cand,
+                                 uint32_t* err, int num_sms, double timeout_s, cudaStream_t s) {
+  // the k of a slot is only known on the device: the configuration that serves every k
+  uint64_t tns = static_cast<uint64_t>((timeout_s > 0 ? timeout_s : 2.0) * 1e9);
+  return launch_cfg<kLargeWarps, kLargeCap>(lib, nullptr, 0, st, cand, nullptr, nullptr, nullptr, err, num_sms, tns,
+                                            false, s, slot);
+}
+
+cudaError_t launch_fallback_pick(const uint64_t* queries, const int32_t* k, const int64_t* out_off, int32_t* oi,
+                                 int32_t* od, int32_t* oc, int Q, ScanSlot* slot, bool first,
+                                 cudaGraphConditionalHandle h, cudaStream_t s) {
+  fallback_pick_kernel<<<1, 32, 0, s>>>(queries, k, out_off, oi, od, oc, Q, slot, first ? 1 : 0, h);
   return cudaGetLastError();
 }
 

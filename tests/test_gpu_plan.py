@@ -52,6 +52,38 @@ def test_learned_plan_and_fallback(gpu_lib):
                 for (gi, gd), (wi, wd) in zip(got, want):
                     assert np.array_equal(gi, wi) and np.array_equal(gd, wd)
                 assert st.fallbacks == nfall
+                assert st.device_fallbacks == nfall          # re-run inside the graph, not by the host
+        finally:
+            fps.fps_batch_plan_release(plan)
+    finally:
+        fps.fps_release(lib)
+
+
+@pytest.mark.parametrize("path_name", ["POPC_BATCH", "TC_FP8"])
+def test_plan_device_fallback_on_candidate_overflow(gpu_lib, path_name):
+    """60,000 copies of one record: a query equal to it accepts them all at distance 0, far more than its
+    candidate region holds, so the select reports it for the exact fallback; the plan's graph re-runs it
+    (WHILE node + indirect single-query scan) and the result is still the oracle's."""
+    fps = gpu_lib
+    x = qstrs(synth.packed(1, 1090))[0]
+    rows = qstrs(synth.packed(40000, 90)) + [x] * 60000 + qstrs(synth.packed(20001, 91))
+    text = synth.strings_to_text(rows)
+    lib = fps.fps_library_load(text=text, flags=fps.FPS_LOAD_TC_OPERAND)
+    try:
+        px = fps.fps_pack_query(x)
+        ks = np.array([30, 1, 1000, 10, 129, 30, 1920, 100], np.int32)
+        plan = fps.fps_batch_plan_create(lib, ks, path=getattr(fps, "FPS_PATH_" + path_name))
+        try:
+            for rep in range(2):
+                qs = synth.packed(len(ks), 1091 + rep)
+                qs[[1, 4, 6]] = px                       # three overflowing queries among ordinary ones
+                st = fps.fps_search_stats()
+                got = fps.fps_batch_plan_run(plan, qs, stats=st)
+                want = oracle.topk_many(text, qstrs(qs), ks)
+                for q, ((gi, gd), (wi, wd)) in enumerate(zip(got, want)):
+                    assert np.array_equal(gi, wi) and np.array_equal(gd, wd), (rep, q)
+                # k = 1 and k = 129 overflow; k = 1920's region (32 k + 8192 keys) holds the 60,000 ties
+                assert st.fallbacks == st.device_fallbacks and st.device_fallbacks >= 2
         finally:
             fps.fps_batch_plan_release(plan)
     finally:

@@ -49,7 +49,8 @@ def parse_args():
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--n", type=int, default=PAPER_N, help="library records")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--workload", default="single", choices=["single", "batch", "learned", "serve", "latency"],
+    p.add_argument("--workload", default="single",
+                   choices=["single", "batch", "learned", "serve", "latency", "shards"],
                    help="single: 16 sequential single queries per step (default); "
                         "batch: --queries queries with mixed k in one batched call per step")
     p.add_argument("--queries", type=int, default=4096)
@@ -692,12 +693,111 @@ def run_serve(args):
         fps.fps_release(lib)
 
 
+def run_shards(args):
+    """The library as three strides (Sec. 2.1: separate datasets searched at once, results combined and
+    sorted): fps_search_shards against the same records loaded as one library."""
+    import threading
+
+    import torch
+
+    import paper_1906_06170_gb300 as fps
+    import synth
+
+    torch.cuda.set_device(0)
+    n = args.n
+    packed = synth.packed(n, 0)
+    cuts = [0, n // 3, 2 * n // 3, n]
+    shards = [fps.fps_library_load(packed=packed[a:b], flags=fps.FPS_LOAD_TC_OPERAND) for a, b in zip(cuts, cuts[1:])]
+    whole = fps.fps_library_load(packed=packed, flags=fps.FPS_LOAD_TC_OPERAND)
+    del packed
+    Q = args.queries
+    qs = synth.packed(Q, synth.query_seed(2))
+    ks = synth.k_mix(Q, seed=2)
+    qd = torch.from_numpy(qs.view(np.int64).copy()).cuda()
+    stream = torch.cuda.current_stream()
+    prog = fps.shard_progress(len(shards))
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / steps * 1e3
+
+    def sharded_tc():
+        fps.fps_search_shards(shards, qd, ks, path=fps.FPS_PATH_TC_FP8, progress=prog, stream=stream)
+
+    def whole_tc():
+        fps.fps_search_batch(whole, qd, ks, path=fps.FPS_PATH_TC_FP8, stream=stream)
+
+    q16 = qd[:QUERIES_PER_STEP].contiguous()
+    k16 = np.full(QUERIES_PER_STEP, K, np.int32)
+
+    def sharded_seq():
+        fps.fps_search_shards(shards, q16, k16, path=fps.FPS_PATH_POPC, stream=stream)
+
+    def whole_seq():
+        fps.fps_search_batch(whole, q16, k16, path=fps.FPS_PATH_POPC, stream=stream)
+
+    clocks = ClockSampler(0)
+    clocks.start()
+    ms_sh = timed(sharded_tc, args.steps, args.warmup)
+    ms_wh = timed(whole_tc, args.steps, args.warmup)
+    ms_sh_seq = timed(sharded_seq, max(args.steps, 20), args.warmup)
+    ms_wh_seq = timed(whole_seq, max(args.steps, 20), args.warmup)
+    clk = clocks.stop()
+    # per-stride progress of one more sharded call, watched from another thread
+    prog.zero_()
+    seen = [None] * len(shards)
+    done = threading.Event()
+
+    def watch(t0):
+        while not done.is_set():
+            v = prog.numpy()
+            for i in range(len(shards)):
+                if seen[i] is None and v[i] == Q:
+                    seen[i] = (time.perf_counter() - t0) * 1e3
+            time.sleep(0.0002)
+
+    t0 = time.perf_counter()
+    th = threading.Thread(target=watch, args=(t0,))
+    th.start()
+    sharded_tc()
+    torch.cuda.synchronize()
+    done.set()
+    th.join()
+    res_sh = fps.fps_search_shards(shards, qs[:64], ks[:64], path=fps.FPS_PATH_TC_FP8)
+    res_wh = fps.fps_search_batch(whole, qs[:64], ks[:64], path=fps.FPS_PATH_TC_FP8)
+    assert all(np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) for a, b in zip(res_sh, res_wh)), \
+        "sharded and whole-library results differ"
+    line = {"metric": METRIC, "value": Q * n / (ms_sh / 1e3) / 1e9, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_sh, "higher_is_better": True, "dtype": "tc_fp8",
+            "data": "synthetic",
+            "whole_library_tc": {"ms_per_step": ms_wh, "value": Q * n / (ms_wh / 1e3) / 1e9},
+            "sequential_16_queries": {"sharded_ms": ms_sh_seq, "whole_ms": ms_wh_seq,
+                                      "sharded_value": QUERIES_PER_STEP * n / (ms_sh_seq / 1e3) / 1e9},
+            "stride_done_ms": seen,
+            "config": {"workload": f"{n:,} generated records (seed 0) as 3 strides of ~{n // 3:,} records, {Q} "
+                                   f"queries (seed 1002) with k from {{1,10,30,100,1000}} per call, tensor-core path "
+                                   f"per stride, device merge; beside: the same records as one library, and 16 "
+                                   f"sequential k={K} queries", "n_records": n, "queries": Q, "strides": 3},
+            "clocks": clk}
+    print(json.dumps(line), flush=True)
+    for lb in shards + [whole]:
+        fps.fps_release(lb)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "latency":
         run_latency(args)
+    elif args.workload == "shards":
+        run_shards(args)
     elif args.workload == "batch":
         run_batch(args)
     elif args.workload == "learned":

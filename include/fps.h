@@ -278,6 +278,31 @@ fps_status fps_mlp_train_step(fps_mlp mlp, const uint64_t* queries, const float*
 fps_status fps_merge_topk(const int32_t* idx, const int32_t* dist, const int64_t* part_off, int parts, int k,
                           int32_t* out_index, int32_t* out_dist, int* out_n);
 
+/*
+ * Several resident libraries searched as one (the paper's parallel strides:
+ * separate datasets searched at the same time, results "combined and
+ * sorted", with each stride's progress shown; Sec. 2.1, Sec. 4.4).  libs[s]
+ * holds the records whose global indices start at index_base[s] (nullable:
+ * the prefix sums of the libraries' sizes, in order); the index ranges must
+ * not overlap.  All libraries live on one device; at most FPS_SHARDS_MAX.
+ * Queries, k, out_offsets and outputs are as in fps_search_batch (host or
+ * device per opts->flags, opts->path per shard); out_index holds global
+ * indices and out_count[q] = min(k[q], total records).  Every shard runs the
+ * batched search into device staging, then one kernel merges the per-shard
+ * lists of each query on the device (k-way merge of ascending (distance,
+ * global index) keys).  progress (nullable) is host memory of n_libs int64
+ * that the device can write: pinned, mapped memory (cudaMallocHost,
+ * cudaHostAlloc), or any host memory on systems whose GPU addresses pageable
+ * memory; FPS_ERR_INVALID_ARG if cudaHostGetDevicePointer refuses it.
+ * progress[s] is set to Q by the device, in stream order, once shard s's
+ * results are complete, so another thread can watch the strides finish.
+ */
+#define FPS_SHARDS_MAX 32
+fps_status fps_search_shards(const fps_library* libs, int n_libs, const int64_t* index_base, const uint64_t* queries,
+                             int Q, const int32_t* k, const int64_t* out_offsets, int32_t* out_index,
+                             int32_t* out_dist, int32_t* out_count, const fps_search_opts* opts, int64_t* progress,
+                             void* cuda_stream);
+
 /* ----------------------------------------------------------------- helpers */
 
 const char* fps_status_string(fps_status st);

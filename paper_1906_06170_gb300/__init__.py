@@ -73,6 +73,8 @@ _lib.fps_search_batch.argtypes = [_vp, _vp, _i32, _vp, _vp, _vp, _vp, _vp, ctype
 _lib.fps_sync.argtypes = [_vp, _vp]
 _lib.fps_search_noalloc.argtypes = [_vp, _vp, _i32, _vp, _vp, _vp, _vp]
 _lib.fps_merge_topk.argtypes = [_vp, _vp, _vp, _i32, _i32, _vp, _vp, ctypes.POINTER(_i32)]
+_lib.fps_search_shards.argtypes = [_vp, _i32, _vp, _vp, _i32, _vp, _vp, _vp, _vp, _vp,
+                                   ctypes.POINTER(fps_search_opts), _vp, _vp]
 _lib.fps_batch_plan_create.argtypes = [_vp, _i32, _vp, _i32, _i32, ctypes.POINTER(_vp)]
 _lib.fps_batch_plan_run.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(fps_search_stats), _vp]
 _lib.fps_batch_plan_release.argtypes = [_vp]
@@ -91,7 +93,7 @@ for _f in ("fps_library_load", "fps_release", "fps_library_info_get", "fps_libra
            "fps_search_packed", "fps_search_batch", "fps_sync", "fps_pack_query", "fps_pack_text", "fps_search_noalloc",
            "fps_mlp_create", "fps_mlp_release", "fps_mlp_set_params", "fps_mlp_get_params", "fps_mlp_predict",
            "fps_mlp_grad", "fps_mlp_train_step", "fps_merge_topk", "fps_batch_plan_create", "fps_batch_plan_run",
-           "fps_batch_plan_release"):
+           "fps_batch_plan_release", "fps_search_shards"):
     getattr(_lib, _f).restype = _i32
 
 
@@ -316,6 +318,61 @@ def fps_search_noalloc(lib: Library, query, k: int, out_index, out_dist, out_cou
                                  out_count.data_ptr(), _stream_ptr(stream))
     _check(st, "fps_search_noalloc")
     return out_index, out_dist, out_count
+
+
+FPS_SHARDS_MAX = 32
+
+
+def shard_progress(n: int):
+    """Pinned host int64[n] (a CPU torch tensor) for fps_search_shards to report per-shard progress into."""
+    import torch
+
+    return torch.zeros(n, dtype=torch.int64, pin_memory=True)
+
+
+def fps_search_shards(libs, queries, k, *, index_base=None, path: int = FPS_PATH_AUTO, out_index=None, out_dist=None,
+                      out_count=None, offsets=None, progress=None, timeout_s: float = 0.0, stream=None, stats=None):
+    """Several resident libraries searched as one, results merged with global indices.
+
+    libs: Library handles; library s holds global indices index_base[s] .. (default: the prefix sums of
+    their sizes).  Forms and outputs as in fps_search_batch.  progress: a tensor from shard_progress();
+    entry s becomes Q once shard s's results are complete.
+    """
+    n = len(libs)
+    harr = (ctypes.c_void_p * max(n, 1))(*[lb._h for lb in libs])
+    base = None if index_base is None else np.ascontiguousarray(np.asarray(index_base, np.int64))
+    Q = int(queries.shape[0]) if hasattr(queries, "shape") else len(queries)
+    kk = np.asarray(k, dtype=np.int32).reshape(-1)
+    if kk.size == 1 and Q != 1:
+        kk = np.full(Q, kk[0], np.int32)
+    kk = np.ascontiguousarray(kk)
+    off = batch_offsets(kk) if offsets is None else np.ascontiguousarray(np.asarray(offsets, np.int64))
+    total = max(int(off[-1]), 1)
+    st_obj = stats if stats is not None else fps_search_stats()
+    prog = progress.data_ptr() if progress is not None else None
+    bptr = base.ctypes.data if base is not None else None
+    if _is_cuda(queries):
+        import torch
+
+        dev = queries.device
+        if out_index is None:
+            out_index = torch.empty(total, dtype=torch.int32, device=dev)
+        if out_dist is None:
+            out_dist = torch.empty(total, dtype=torch.int32, device=dev)
+        if out_count is None:
+            out_count = torch.empty(max(Q, 1), dtype=torch.int32, device=dev)
+        o = _opts(path, FPS_SEARCH_DEVICE_IO, timeout_s, st_obj)
+        _check(_lib.fps_search_shards(harr, n, bptr, queries.data_ptr(), Q, kk.ctypes.data, off.ctypes.data,
+                                      out_index.data_ptr(), out_dist.data_ptr(), out_count.data_ptr(), ctypes.byref(o),
+                                      prog, _stream_ptr(stream)), "fps_search_shards")
+        return out_index, out_dist, out_count, off
+    q = np.ascontiguousarray(np.asarray(queries, dtype=np.uint64).reshape(-1, FPS_WORDS))
+    idx, dist, cnt = np.zeros(total, np.int32), np.zeros(total, np.int32), np.zeros(max(Q, 1), np.int32)
+    o = _opts(path, 0, timeout_s, st_obj)
+    _check(_lib.fps_search_shards(harr, n, bptr, q.ctypes.data, Q, kk.ctypes.data, off.ctypes.data, idx.ctypes.data,
+                                  dist.ctypes.data, cnt.ctypes.data, ctypes.byref(o), prog, _stream_ptr(stream)),
+           "fps_search_shards")
+    return [(idx[off[i]: off[i] + cnt[i]].copy(), dist[off[i]: off[i] + cnt[i]].copy()) for i in range(Q)]
 
 
 def fps_merge_topk(parts, k: int):

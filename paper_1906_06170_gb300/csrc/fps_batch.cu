@@ -438,4 +438,65 @@ cudaError_t batch_select(const DevLib& lib, const BatchDev& b, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+namespace {
+
+// ------------------------------------------------------------- shard merge
+// One warp per query: lane s holds the head of shard s's ascending list; each
+// round the smallest key (distance << 32 | global index) over the lanes is
+// written and its lane advances.  Indices of different shards never collide,
+// so the keys are distinct and the order is the total (distance, index) order.
+__global__ void shard_merge_kernel(ShardLists sl, int Q, const int64_t* __restrict__ off, int32_t* __restrict__ out_idx,
+                                   int32_t* __restrict__ out_dist, int32_t* __restrict__ out_count) {
+  const int lane = threadIdx.x & 31;
+  const int q = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (q >= Q) return;
+  const int64_t o = off[q];
+  const int kq = static_cast<int>(off[q + 1] - o);
+  int cnt = 0, p = 0;
+  if (lane < sl.n) cnt = sl.count[lane][q];
+  auto key_at = [&](int i) -> unsigned long long {
+    return (static_cast<unsigned long long>(static_cast<uint32_t>(sl.dist[lane][o + i])) << 32) |
+           static_cast<uint32_t>(sl.base[lane] + sl.idx[lane][o + i]);
+  };
+  unsigned long long head = (lane < sl.n && p < cnt) ? key_at(p) : ~0ull;
+  int n_out = 0;
+  for (; n_out < kq; ++n_out) {
+    unsigned long long m = head;
+#pragma unroll
+    for (int sh = 16; sh > 0; sh >>= 1) {
+      const unsigned long long other = __shfl_xor_sync(kFull, m, sh);
+      m = other < m ? other : m;
+    }
+    if (m == ~0ull) break;
+    if (lane == 0) {
+      out_idx[o + n_out] = static_cast<int32_t>(m & 0xFFFFFFFFull);
+      out_dist[o + n_out] = static_cast<int32_t>(m >> 32);
+    }
+    if (head == m) {
+      ++p;
+      head = p < cnt ? key_at(p) : ~0ull;
+    }
+  }
+  if (lane == 0) out_count[q] = n_out;
+}
+
+__global__ void progress_kernel(int64_t* slot, int64_t value) {
+  if (threadIdx.x == 0) *reinterpret_cast<volatile int64_t*>(slot) = value;
+}
+
+}  // namespace
+
+cudaError_t launch_shard_merge(const ShardLists& sl, int Q, const int64_t* off, int32_t* out_idx, int32_t* out_dist,
+                               int32_t* out_count, cudaStream_t s) {
+  if (Q <= 0) return cudaSuccess;
+  const int warps = 8;
+  shard_merge_kernel<<<(Q + warps - 1) / warps, 32 * warps, 0, s>>>(sl, Q, off, out_idx, out_dist, out_count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_progress(int64_t* slot_dev, int64_t value, cudaStream_t s) {
+  progress_kernel<<<1, 32, 0, s>>>(slot_dev, value);
+  return cudaGetLastError();
+}
+
 }  // namespace fps

@@ -197,6 +197,8 @@ void free_library(Library* L) {
     if (w->io_host) cudaFreeHost(w->io_host);
     if (w->batch_block) cudaFree(w->batch_block);
     if (w->batch_host) cudaFreeHost(w->batch_host);
+    if (w->shard_block) cudaFree(w->shard_block);
+    if (w->shard_host) cudaFreeHost(w->shard_host);
     delete w;
   }
   L->ws.clear();
@@ -476,6 +478,26 @@ fps_status search_one_host(Library* L, const uint64_t q[3], int k, int32_t* out_
   return FPS_OK;
 }
 
+
+// Grow a device (or pinned host) block to at least `need` bytes.  cudaFree waits for the
+// device, so work still reading the old block has finished before it goes.
+fps_status grow_block(void** block, size_t* have, size_t need, bool host) {
+  if (*have >= need) return FPS_OK;
+  if (*block) {
+    if (host)
+      cudaFreeHost(*block);
+    else
+      cudaFree(*block);
+  }
+  *block = nullptr;
+  *have = 0;
+  if ((host ? cudaMallocHost(block, need) : cudaMalloc(block, need)) != cudaSuccess) {
+    cudaGetLastError();
+    return FPS_ERR_CUDA;
+  }
+  *have = need;
+  return FPS_OK;
+}
 
 // Grow the per-stream batch staging (device block and pinned host block).
 fps_status batch_staging(Workspace* w, size_t dev_bytes, size_t host_bytes) {
@@ -1145,6 +1167,148 @@ fps_status fps_search_batch(fps_library lib, const uint64_t* queries, int Q, con
   if (!g.ok) return FPS_ERR_CUDA;
   const bool dev_io = opts && (opts->flags & FPS_SEARCH_DEVICE_IO);
   return search_batch_impl(L, queries, Q, k, out_offsets, total, out_index, out_dist, out_count, opts, dev_io, s);
+}
+
+fps_status fps_search_shards(const fps_library* libs, int n_libs, const int64_t* index_base, const uint64_t* queries,
+                             int Q, const int32_t* k, const int64_t* out_offsets, int32_t* out_index,
+                             int32_t* out_dist, int32_t* out_count, const fps_search_opts* opts, int64_t* progress,
+                             void* cuda_stream) {
+  if (!libs || n_libs <= 0 || n_libs > kShardsMax || Q < 0 ||
+      (Q > 0 && (!queries || !k || !out_offsets || !out_index || !out_dist || !out_count)))
+    return FPS_ERR_INVALID_ARG;
+  if (n_libs > FPS_SHARDS_MAX) return FPS_ERR_INVALID_ARG;
+  std::vector<Library*> Ls(n_libs);
+  std::vector<int64_t> base(n_libs);
+  int64_t acc = 0;
+  for (int i = 0; i < n_libs; ++i) {
+    if (!libs[i]) return FPS_ERR_INVALID_ARG;
+    Ls[i] = reinterpret_cast<Library*>(libs[i]);
+    if (Ls[i]->device != Ls[0]->device) return FPS_ERR_INVALID_ARG;
+    base[i] = index_base ? index_base[i] : acc;
+    acc += Ls[i]->n;
+    if (base[i] < 0 || base[i] + Ls[i]->n > static_cast<int64_t>(INT32_MAX)) return FPS_ERR_INVALID_ARG;
+  }
+  {  // the global index ranges must be disjoint
+    std::vector<std::pair<int64_t, int64_t>> r;
+    for (int i = 0; i < n_libs; ++i)
+      if (Ls[i]->n > 0) r.emplace_back(base[i], base[i] + Ls[i]->n);
+    std::sort(r.begin(), r.end());
+    for (size_t i = 1; i < r.size(); ++i)
+      if (r[i].first < r[i - 1].second) return FPS_ERR_INVALID_ARG;
+  }
+  int64_t total = 0;
+  for (int q = 0; q < Q; ++q) {
+    fps_status st = check_k(k[q]);
+    if (st != FPS_OK) return st;
+    if (out_offsets[q] < 0 || out_offsets[q + 1] - out_offsets[q] < k[q]) return FPS_ERR_INVALID_ARG;
+    total = std::max<int64_t>(total, out_offsets[q + 1]);
+  }
+  if (Q == 0) return FPS_OK;
+  Library* L0 = Ls[0];
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  DeviceGuard g(L0->device);
+  if (!g.ok) return FPS_ERR_CUDA;
+  const bool dev_io = opts && (opts->flags & FPS_SEARCH_DEVICE_IO);
+  if (!dev_io)
+    for (int q = 0; q < Q; ++q)
+      if (queries[3 * q + 2] >> (kBits - 128)) return FPS_ERR_INVALID_ARG;
+  int64_t* prog_dev = nullptr;
+  if (progress && cudaHostGetDevicePointer(reinterpret_cast<void**>(&prog_dev), progress, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return FPS_ERR_INVALID_ARG;   // not pinned, device-mapped host memory
+  }
+  Workspace* w = nullptr;
+  fps_status st = get_workspace(L0, s, &w);
+  if (st != FPS_OK) return st;
+  // device staging: [offsets Q+1][queries Q*3 (host form)][per shard: index, dist (total each), count Q]
+  //                 [merged index, dist, count (host form)]
+  Carve cv;
+  const size_t d_off = cv.take(sizeof(int64_t) * (Q + 1));
+  const size_t d_q = cv.take(dev_io ? 0 : sizeof(uint64_t) * 3 * Q);
+  std::vector<size_t> d_si(n_libs), d_sd(n_libs), d_sc(n_libs);
+  for (int i = 0; i < n_libs; ++i) {
+    d_si[i] = cv.take(sizeof(int32_t) * std::max<int64_t>(total, 1));
+    d_sd[i] = cv.take(sizeof(int32_t) * std::max<int64_t>(total, 1));
+    d_sc[i] = cv.take(sizeof(int32_t) * Q);
+  }
+  const size_t d_mi = cv.take(dev_io ? 0 : sizeof(int32_t) * std::max<int64_t>(total, 1));
+  const size_t d_md = cv.take(dev_io ? 0 : sizeof(int32_t) * std::max<int64_t>(total, 1));
+  const size_t d_mc = cv.take(dev_io ? 0 : sizeof(int32_t) * Q);
+  const size_t h_bytes = cv.at;   // pinned mirror of the same layout (offsets, queries, merged results)
+  st = grow_block(&w->shard_block, &w->shard_bytes, cv.at, false);
+  if (st == FPS_OK) st = grow_block(&w->shard_host, &w->shard_host_bytes, h_bytes, true);
+  if (st != FPS_OK) return st;
+  char* db = static_cast<char*>(w->shard_block);
+  char* hb = static_cast<char*>(w->shard_host);
+  std::memcpy(hb + d_off, out_offsets, sizeof(int64_t) * (Q + 1));
+  if (!dev_io) std::memcpy(hb + d_q, queries, sizeof(uint64_t) * 3 * Q);
+  if (cudaMemcpyAsync(db, hb, dev_io ? d_q : d_q + sizeof(uint64_t) * 3 * Q, cudaMemcpyHostToDevice, s) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return FPS_ERR_CUDA;
+  }
+  const uint64_t* qdev = dev_io ? queries : reinterpret_cast<const uint64_t*>(db + d_q);
+  fps_search_opts so{};
+  if (opts) so = *opts;
+  so.flags |= FPS_SEARCH_DEVICE_IO;
+  fps_search_stats shard_stats{};
+  so.stats = &shard_stats;
+  int64_t fallbacks = 0, candidates = 0, path_used = 0;
+  ShardLists sl{};
+  sl.n = n_libs;
+  for (int i = 0; i < n_libs; ++i) {
+    int32_t* si = reinterpret_cast<int32_t*>(db + d_si[i]);
+    int32_t* sd = reinterpret_cast<int32_t*>(db + d_sd[i]);
+    int32_t* sc = reinterpret_cast<int32_t*>(db + d_sc[i]);
+    shard_stats = fps_search_stats{};
+    DeviceGuard gi(Ls[i]->device);
+    st = search_batch_impl(Ls[i], qdev, Q, k, out_offsets, total, si, sd, sc, &so, true, s);
+    if (st != FPS_OK) return st;
+    fallbacks += shard_stats.fallbacks;
+    candidates += shard_stats.candidates;
+    path_used = shard_stats.path_used;
+    if (prog_dev && launch_progress(prog_dev + i, Q, s) != cudaSuccess) {
+      cudaGetLastError();
+      return FPS_ERR_CUDA;
+    }
+    sl.idx[i] = si;
+    sl.dist[i] = sd;
+    sl.count[i] = sc;
+    sl.base[i] = base[i];
+  }
+  int32_t* mi = dev_io ? out_index : reinterpret_cast<int32_t*>(db + d_mi);
+  int32_t* md = dev_io ? out_dist : reinterpret_cast<int32_t*>(db + d_md);
+  int32_t* mc = dev_io ? out_count : reinterpret_cast<int32_t*>(db + d_mc);
+  if (launch_shard_merge(sl, Q, reinterpret_cast<const int64_t*>(db + d_off), mi, md, mc, s) != cudaSuccess) {
+    cudaGetLastError();
+    return FPS_ERR_CUDA;
+  }
+  if (!dev_io) {
+    if (cudaMemcpyAsync(hb + d_mi, db + d_mi, d_mc + sizeof(int32_t) * Q - d_mi, cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+      cudaGetLastError();
+      return FPS_ERR_CUDA;
+    }
+    for (int i = 0; i < n_libs; ++i) {   // a device-side failure in any shard's searches
+      Workspace* wi = nullptr;
+      DeviceGuard gi(Ls[i]->device);
+      st = get_workspace(Ls[i], s, &wi);
+      if (st == FPS_OK) st = take_device_error(wi, s);
+      if (st != FPS_OK) return st;
+    }
+    std::memcpy(out_index, hb + d_mi, sizeof(int32_t) * total);
+    std::memcpy(out_dist, hb + d_md, sizeof(int32_t) * total);
+    std::memcpy(out_count, hb + d_mc, sizeof(int32_t) * Q);
+  }
+  if (opts && opts->stats) {
+    opts->stats->queries = Q;
+    opts->stats->fallbacks = fallbacks;
+    opts->stats->device_fallbacks = 0;
+    opts->stats->candidates = candidates;
+    opts->stats->path_used = path_used;
+  }
+  return FPS_OK;
 }
 
 fps_status fps_merge_topk(const int32_t* idx, const int32_t* dist, const int64_t* part_off, int parts, int k,

@@ -83,6 +83,11 @@ struct Workspace {
   size_t batch_bytes = 0;
   void* batch_host = nullptr;
   size_t batch_host_bytes = 0;
+  // shard-search staging (grown on demand)
+  void* shard_block = nullptr;
+  size_t shard_bytes = 0;
+  void* shard_host = nullptr;
+  size_t shard_host_bytes = 0;
 };
 
 struct Library {
@@ -132,6 +137,22 @@ cudaError_t batch_thr_from_tau(const BatchDev& b, const float* tau, cudaStream_t
 cudaError_t batch_scan_popc(const DevLib& lib, const BatchDev& b, int num_sms, uint32_t* work_counter,
                             cudaStream_t s);
 cudaError_t batch_select(const DevLib& lib, const BatchDev& b, cudaStream_t s);
+
+// ---- shard merge (fps_batch.cu): per-shard result lists of one batch (device memory, laid out
+// by the batch's output offsets) and the global index of each shard's first record
+constexpr int kShardsMax = 32;
+struct ShardLists {
+  int n;
+  const int32_t* idx[kShardsMax];
+  const int32_t* dist[kShardsMax];
+  const int32_t* count[kShardsMax];
+  int64_t base[kShardsMax];
+};
+// out_count[q] = entries written for query q (<= off[q+1] - off[q])
+cudaError_t launch_shard_merge(const ShardLists& sl, int Q, const int64_t* off, int32_t* out_idx, int32_t* out_dist,
+                               int32_t* out_count, cudaStream_t s);
+// *slot_dev = value, in stream order (slot_dev: device view of pinned host memory)
+cudaError_t launch_progress(int64_t* slot_dev, int64_t value, cudaStream_t s);
 
 // ---- tensor-core batched scan (fps_tc.cu)
 size_t tc_operand_bytes(int64_t n_tiles128);

@@ -65,6 +65,7 @@ def _load():
             lib.oracle_topk.argtypes = [vp, sz, u32, ctypes.c_char_p, i64, i32, vp, vp, vp, vp, vp]
             lib.oracle_topk_many.argtypes = [vp, sz, u32, ctypes.c_char_p, i64, vp, vp, i32, vp, vp, vp, vp]
             lib.oracle_combine.argtypes = [vp, vp, i64, i64, vp, vp, vp]
+            lib.oracle_wide_topk.argtypes = [vp, sz, i32, ctypes.c_char_p, i64, i32, i32, vp, vp, vp, vp, vp]
             for f in (lib.oracle_count, lib.oracle_distances, lib.oracle_cids, lib.oracle_topk,
                       lib.oracle_topk_many, lib.oracle_combine):
                 f.restype = i32
@@ -199,3 +200,29 @@ def fig3_topk(rows, query: str, k: int):
     K = np.abs(C).sum(axis=1)
     order = np.argsort(K, kind="stable")[: max(int(k), 0)]
     return order.astype(np.int32), K[order].astype(np.int32)
+
+
+# ------------------------------------------------------------------ wide
+MANHATTAN, TANIMOTO = 0, 1
+
+
+def wide_topk(text, n_bits: int, query: str, k: int, metric: int = MANHATTAN, threads=None):
+    """Top-k rows of a wide library (lines of n_bits '0'/'1' characters).
+
+    Manhattan: ascending d = number of differing characters; Tanimoto: descending c / u
+    (c = both '1', u = either '1'; 1 when u = 0), compared exactly.  Ties: ascending row.
+    Returns (rows, num, den): Manhattan num = d, den = 1; Tanimoto num = c, den = u."""
+    lib = _load()
+    p, n, keep = _buf(text)
+    q = query.encode() if isinstance(query, str) else bytes(query)
+    if len(q) != n_bits:
+        raise OracleError(ERR_ARG)
+    m = max(int(k), 1)
+    idx, num, den = np.zeros(m, np.int32), np.zeros(m, np.int32), np.zeros(m, np.int32)
+    out, err = ctypes.c_int64(0), ctypes.c_int64(0)
+    st = lib.oracle_wide_topk(p, n, int(n_bits), q, int(k), int(metric), _threads(threads), idx.ctypes.data,
+                              num.ctypes.data, den.ctypes.data, ctypes.byref(out), ctypes.byref(err))
+    if st:
+        raise OracleError(st, err.value)
+    c = out.value
+    return idx[:c], num[:c], den[:c]

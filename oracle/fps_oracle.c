@@ -304,3 +304,142 @@ int oracle_combine(const int32_t* idx, const int32_t* dist, int64_t n, int64_t k
   free(pr);
   return ORACLE_OK;
 }
+
+/* ====================================================================== wide
+ * Longer fingerprints and the Tanimoto measure (an extension beyond the
+ * paper's 166 MACCS keys: its conclusion names more features as future work).
+ * A wide library is text of lines of exactly n_bits '0'/'1' characters (a
+ * trailing '\r' is dropped; no CID column).  Per row, on the characters:
+ *   ORACLE_MANHATTAN: d = #{j : q_j != x_j}, ranked ascending;
+ *   ORACLE_TANIMOTO:  c = #{j : q_j = x_j = '1'}, u = #{j : q_j = '1' or
+ *                     x_j = '1'}, similarity c / u (1 when u = 0: two empty
+ *                     sets are equal), ranked descending; two similarities are
+ *                     compared exactly as c1 u2 vs c2 u1.
+ * Ties are ranked by ascending 0-based row.  Outputs per result: row, and the
+ * measure as num / den (Manhattan: d / 1; Tanimoto: c / u, with 0 / 0 for u = 0).
+ * All rows are scored (several threads over contiguous ranges), then one full
+ * qsort orders them. */
+#define ORACLE_MANHATTAN 0
+#define ORACLE_TANIMOTO 1
+
+typedef struct {
+  int32_t num, den, i;
+} wpair_t;
+
+typedef struct {
+  const char* text;
+  const int64_t* line_start;
+  const char* q;
+  int n_bits, metric;
+  wpair_t* out;
+  int64_t lo, hi;
+} wjob_t;
+
+static void* wide_job(void* arg) {
+  wjob_t* jb = (wjob_t*)arg;
+  for (int64_t i = jb->lo; i < jb->hi; ++i) {
+    const char* x = jb->text + jb->line_start[i];
+    int32_t a = 0, b = 0;
+    if (jb->metric == ORACLE_MANHATTAN) {
+      for (int j = 0; j < jb->n_bits; ++j) a += (x[j] != jb->q[j]);
+      b = 1;
+    } else {
+      for (int j = 0; j < jb->n_bits; ++j) {
+        const int qj = jb->q[j] == '1', xj = x[j] == '1';
+        a += qj & xj;
+        b += qj | xj;
+      }
+    }
+    jb->out[i] = (wpair_t){a, b, (int32_t)i};
+  }
+  return NULL;
+}
+
+/* Tanimoto order: larger c/u first (u = 0 counts as 1), then smaller row. */
+static int tanimoto_cmp(const void* pa, const void* pb) {
+  const wpair_t* x = (const wpair_t*)pa;
+  const wpair_t* y = (const wpair_t*)pb;
+  const int64_t xn = x->den ? x->num : 1, xd = x->den ? x->den : 1;
+  const int64_t yn = y->den ? y->num : 1, yd = y->den ? y->den : 1;
+  const int64_t l = xn * yd, r = yn * xd;
+  if (l != r) return l > r ? -1 : 1;
+  if (x->i != y->i) return x->i < y->i ? -1 : 1;
+  return 0;
+}
+
+static int manhattan_cmp(const void* pa, const void* pb) {
+  const wpair_t* x = (const wpair_t*)pa;
+  const wpair_t* y = (const wpair_t*)pb;
+  if (x->num != y->num) return x->num < y->num ? -1 : 1;
+  if (x->i != y->i) return x->i < y->i ? -1 : 1;
+  return 0;
+}
+
+int oracle_wide_topk(const char* text, size_t len, int n_bits, const char* query, int64_t k, int metric,
+                     int nthreads, int32_t* out_idx, int32_t* out_num, int32_t* out_den, int64_t* out_n,
+                     int64_t* err_line) {
+  if (!text && len) return ORACLE_ERR_ARG;
+  if (!query || n_bits < 1 || k < 0 || (metric != ORACLE_MANHATTAN && metric != ORACLE_TANIMOTO))
+    return ORACLE_ERR_ARG;
+  if (!all01(query, n_bits)) return ORACLE_ERR_ARG;
+  /* rows: every line must be n_bits '0'/'1' characters (optionally followed by '\r') */
+  int64_t cap = 1024, n = 0;
+  int64_t* ls = (int64_t*)malloc(sizeof(int64_t) * (size_t)cap);
+  if (!ls) return ORACLE_ERR_NOMEM;
+  size_t p = 0;
+  while (p < len) {
+    size_t e = p;
+    while (e < len && text[e] != '\n') ++e;
+    size_t l = e - p;
+    if (l > 0 && text[p + l - 1] == '\r') --l;
+    if ((int64_t)l != n_bits || !all01(text + p, (int64_t)l)) {
+      if (err_line) *err_line = n + 1;
+      free(ls);
+      return ORACLE_ERR_PARSE;
+    }
+    if (n == cap) {
+      cap *= 2;
+      int64_t* g = (int64_t*)realloc(ls, sizeof(int64_t) * (size_t)cap);
+      if (!g) {
+        free(ls);
+        return ORACLE_ERR_NOMEM;
+      }
+      ls = g;
+    }
+    ls[n++] = (int64_t)p;
+    p = e + 1;
+  }
+  wpair_t* pr = (wpair_t*)malloc(sizeof(wpair_t) * (size_t)(n ? n : 1));
+  if (!pr) {
+    free(ls);
+    return ORACLE_ERR_NOMEM;
+  }
+  if (nthreads < 1) nthreads = 1;
+  if (nthreads > 256) nthreads = 256;
+  if (n < 4096) nthreads = 1;
+  pthread_t th[256];
+  int started[256];
+  wjob_t jobs[256];
+  int64_t chunk = (n + nthreads - 1) / nthreads;
+  for (int t = 0; t < nthreads; ++t) {
+    int64_t lo = chunk * t, hi = lo + chunk;
+    if (lo > n) lo = n;
+    if (hi > n) hi = n;
+    jobs[t] = (wjob_t){text, ls, query, n_bits, metric, pr, lo, hi};
+    started[t] = nthreads > 1 && pthread_create(&th[t], NULL, wide_job, &jobs[t]) == 0;
+    if (!started[t]) wide_job(&jobs[t]);
+  }
+  for (int t = 0; t < nthreads; ++t)
+    if (started[t]) pthread_join(th[t], NULL);
+  qsort(pr, (size_t)n, sizeof(wpair_t), metric == ORACLE_MANHATTAN ? manhattan_cmp : tanimoto_cmp);
+  int64_t m = k < n ? k : n;
+  for (int64_t r = 0; r < m; ++r) {
+    out_idx[r] = pr[r].i;
+    out_num[r] = pr[r].num;
+    out_den[r] = pr[r].den;
+  }
+  *out_n = m;
+  free(pr);
+  free(ls);
+  return ORACLE_OK;
+}

@@ -57,6 +57,10 @@ def _load():
             lib.synth_packed_at.argtypes = [u64, u64, vp, u64, vp]
             lib.synth_draw.argtypes = [u64, u64, u64]
             lib.synth_draw.restype = u64
+            lib.synth_wide.argtypes = [u64, u64, u64, u64, i32, i32, vp, vp]
+            lib.synth_wide.restype = i32
+            lib.synth_wide_at.argtypes = [u64, u64, vp, u64, i32, vp]
+            lib.synth_wide_at.restype = i32
             _lib = lib
     return _lib
 
@@ -151,3 +155,41 @@ def k_mix(q: int, seed: int = 2, choices=(1, 10, 30, 100, 1000)) -> np.ndarray:
 def query_seed(config_id: int) -> int:
     """Seed of the generated query set for workload `config_id` (1000 + id)."""
     return 1000 + int(config_id)
+
+
+# ------------------------------------------------------------------ wide
+def wide_words(n_bits: int) -> int:
+    return (int(n_bits) + 63) // 64
+
+
+def wide_packed(n: int, n_bits: int, seed: int, start: int = 0, chem_seed: int = 0, threads=None) -> np.ndarray:
+    """Records [start, start+n) of a wide library (n_bits per record): uint64 [n, W], bits past n_bits zero."""
+    out = np.zeros((int(n), wide_words(n_bits)), np.uint64)
+    if _load().synth_wide(chem_seed, seed, start, int(n), int(n_bits), _threads(threads), out.ctypes.data, None):
+        raise ValueError("n_bits must be in 1..4096")
+    return out
+
+
+def wide_text(n: int, n_bits: int, seed: int, start: int = 0, chem_seed: int = 0, threads=None) -> bytes:
+    """The same records as n lines of n_bits '0'/'1' characters plus '\n'."""
+    buf = ctypes.create_string_buffer(int(n) * (int(n_bits) + 1))
+    if _load().synth_wide(chem_seed, seed, start, int(n), int(n_bits), _threads(threads), None, buf):
+        raise ValueError("n_bits must be in 1..4096")
+    return buf.raw
+
+
+def wide_at(idx, n_bits: int, seed: int, chem_seed: int = 0) -> np.ndarray:
+    """Wide records chosen by index (e.g. queries that are library members)."""
+    idx = np.ascontiguousarray(np.asarray(idx, np.uint64).reshape(-1))
+    out = np.zeros((idx.size, wide_words(n_bits)), np.uint64)
+    if _load().synth_wide_at(chem_seed, seed, idx.ctypes.data, idx.size, int(n_bits), out.ctypes.data):
+        raise ValueError("n_bits must be in 1..4096")
+    return out
+
+
+def wide_to_strings(words: np.ndarray, n_bits: int) -> list:
+    """Format packed wide records as n_bits-character '0'/'1' strings (character j = word j//64, bit j%64)."""
+    W = wide_words(n_bits)
+    words = np.asarray(words, dtype=np.uint64).reshape(-1, W)
+    bits = np.unpackbits(words.view(np.uint8).reshape(-1, W * 8), axis=1, bitorder="little")[:, :n_bits]
+    return ["".join("1" if b else "0" for b in row) for row in bits]

@@ -174,3 +174,124 @@ void synth_packed_at(uint64_t chem_seed, uint64_t seed, const uint64_t* idx, uin
 
 /* A raw uniform 64-bit draw, for seeded choices made by callers (query picks, k mixes, arrivals). */
 uint64_t synth_draw(uint64_t seed, uint64_t rec, uint64_t slot) { return draw(seed, rec, slot); }
+
+/* ------------------------------------------------------------------ wide
+ * Longer fingerprints (n_bits up to 4096, W = ceil(n_bits / 64) words, bits
+ * past n_bits zero), for the n-bit / Tanimoto search.  Same SplitMix64 draws;
+ * the density is that of hashed circular fingerprints rather than MACCS keys:
+ *   - p_j ~ Beta(0.5, 8) for every bit j (mean ~ 0.059), rounded to 2^-20:
+ *     X = Z^2/2 (Z from Box-Muller), Y = -ln(U1 ... U8), p = X / (X + Y), the
+ *     ten uniforms of bit j drawn from the chemistry seed at record
+ *     0xFFFFF0 - (j >> 8), slots 16 (j & 255) .. +9;
+ *   - record i: bit j = [32-bit half (j & 1) of draw(seed, i, j >> 1) < T_j];
+ *   - 1 % planted near-duplicates (decision slot 3000, source 3001, count
+ *     3002, positions 3003...): a copy of an earlier record with m ~ U{1..5}
+ *     distinct bits flipped anywhere in [0, n_bits). */
+#define WIDE_MAX_BITS 4096
+
+void synth_wide_thresholds(uint64_t chem_seed, int n_bits, uint32_t* T) {
+  const double two_pi = 6.283185307179586476925286766559;
+  for (int j = 0; j < n_bits; ++j) {
+    const uint64_t rec = 0xFFFFF0ull - (uint64_t)(j >> 8), sl = 16 * (uint64_t)(j & 255);
+    double u1 = unit_open(draw(chem_seed, rec, sl + 0));
+    double u2 = unit_open(draw(chem_seed, rec, sl + 1));
+    double y = 0.0;
+    for (int t = 0; t < 8; ++t) y -= log(unit_open(draw(chem_seed, rec, sl + 2 + (uint64_t)t)));
+    double z = sqrt(-2.0 * log(u1)) * cos(two_pi * u2);
+    double x = 0.5 * z * z;
+    double pj = (x + y) > 0.0 ? x / (x + y) : 0.0;
+    double q = floor(pj * 1048576.0 + 0.5);
+    if (q >= 1048576.0) q = 1048575.0;
+    if (q < 0.0) q = 0.0;
+    T[j] = (uint32_t)q << 12;
+  }
+}
+
+static void gen_wide(const uint32_t* T, int n_bits, uint64_t seed, uint64_t i, uint64_t* w) {
+  const int W = (n_bits + 63) / 64;
+  if (i > 0 && draw(seed, i, 3000) % 100ULL == 0ULL) {
+    gen_wide(T, n_bits, seed, draw(seed, i, 3001) % i, w);
+    const int m = 1 + (int)(draw(seed, i, 3002) % 5ULL);
+    int pos[5], got = 0;
+    for (uint64_t t = 0; got < m; ++t) {
+      int cand = (int)(draw(seed, i, 3003 + t) % (uint64_t)n_bits);
+      int dup = 0;
+      for (int a = 0; a < got; ++a) dup |= (pos[a] == cand);
+      if (!dup) pos[got++] = cand;
+    }
+    for (int a = 0; a < m; ++a) w[pos[a] >> 6] ^= 1ULL << (pos[a] & 63);
+    return;
+  }
+  for (int a = 0; a < W; ++a) w[a] = 0;
+  for (int s = 0; 2 * s < n_bits; ++s) {
+    uint64_t h = draw(seed, i, (uint64_t)s);
+    int j0 = 2 * s, j1 = 2 * s + 1;
+    if ((uint32_t)(h & 0xFFFFFFFFu) < T[j0]) w[j0 >> 6] |= 1ULL << (j0 & 63);
+    if (j1 < n_bits && (uint32_t)(h >> 32) < T[j1]) w[j1 >> 6] |= 1ULL << (j1 & 63);
+  }
+}
+
+typedef struct {
+  const uint32_t* T;
+  int n_bits;
+  uint64_t seed, start, begin, end;
+  uint64_t* packed;
+  char* text;
+} wjob_t;
+
+static void* run_wjob(void* arg) {
+  wjob_t* jb = (wjob_t*)arg;
+  const int W = (jb->n_bits + 63) / 64;
+  uint64_t w[WIDE_MAX_BITS / 64];
+  for (uint64_t r = jb->begin; r < jb->end; ++r) {
+    gen_wide(jb->T, jb->n_bits, jb->seed, jb->start + r, w);
+    if (jb->packed) memcpy(jb->packed + (size_t)W * r, w, sizeof(uint64_t) * W);
+    if (jb->text) {
+      char* line = jb->text + (size_t)r * (jb->n_bits + 1);
+      for (int j = 0; j < jb->n_bits; ++j) line[j] = (char)('0' + ((w[j >> 6] >> (j & 63)) & 1ULL));
+      line[jb->n_bits] = '\n';
+    }
+  }
+  return NULL;
+}
+
+/* Records [start, start+n) of wide library `seed`: packed (W words each) and/or text (n_bits + 1 bytes each).
+   Returns 0, or -1 if n_bits is outside 1..4096. */
+int synth_wide(uint64_t chem_seed, uint64_t seed, uint64_t start, uint64_t n, int n_bits, int nthreads,
+               uint64_t* packed, char* text) {
+  if (n_bits < 1 || n_bits > WIDE_MAX_BITS) return -1;
+  uint32_t* T = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)n_bits);
+  if (!T) return -1;
+  synth_wide_thresholds(chem_seed, n_bits, T);
+  if (nthreads < 1) nthreads = 1;
+  if (nthreads > 256) nthreads = 256;
+  if ((uint64_t)nthreads > n) nthreads = n ? (int)n : 1;
+  pthread_t th[256];
+  int started[256];
+  wjob_t jobs[256];
+  uint64_t chunk = (n + nthreads - 1) / nthreads;
+  for (int t = 0; t < nthreads; ++t) {
+    uint64_t b = chunk * t, e = b + chunk;
+    if (b > n) b = n;
+    if (e > n) e = n;
+    jobs[t] = (wjob_t){T, n_bits, seed, start, b, e, packed, text};
+    started[t] = nthreads > 1 && pthread_create(&th[t], NULL, run_wjob, &jobs[t]) == 0;
+    if (!started[t]) run_wjob(&jobs[t]);
+  }
+  for (int t = 0; t < nthreads; ++t)
+    if (started[t]) pthread_join(th[t], NULL);
+  free(T);
+  return 0;
+}
+
+/* Wide records chosen by index. */
+int synth_wide_at(uint64_t chem_seed, uint64_t seed, const uint64_t* idx, uint64_t n, int n_bits, uint64_t* out) {
+  if (n_bits < 1 || n_bits > WIDE_MAX_BITS) return -1;
+  uint32_t* T = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)n_bits);
+  if (!T) return -1;
+  synth_wide_thresholds(chem_seed, n_bits, T);
+  const int W = (n_bits + 63) / 64;
+  for (uint64_t r = 0; r < n; ++r) gen_wide(T, n_bits, seed, idx[r], out + (size_t)W * r);
+  free(T);
+  return 0;
+}

@@ -303,6 +303,37 @@ fps_status fps_search_shards(const fps_library* libs, int n_libs, const int64_t*
                              int32_t* out_dist, int32_t* out_count, const fps_search_opts* opts, int64_t* progress,
                              void* cuda_stream);
 
+/*
+ * Longer fingerprints (an extension beyond the paper's 166 MACCS keys; its
+ * conclusion names more features as future work): records of n_bits bits
+ * (1..FPS_WIDE_MAX_BITS), W = ceil(n_bits / 64) words each, bit j of a record
+ * = word j/64, bit j%64 (bits past n_bits zero).  Two measures:
+ *   FPS_METRIC_MANHATTAN  d = popc(q XOR x), ascending;
+ *   FPS_METRIC_TANIMOTO   c / u with c = popc(q AND x), u = popc(q OR x)
+ *                         (1 when u = 0), descending, compared exactly;
+ * ties by ascending record index.  The library is resident in device memory
+ * (word-major tiles of 128 records; no popcount buckets) until released.
+ * fps_wide_load takes text (lines of n_bits '0'/'1' characters; a trailing
+ * '\r' is dropped; FPS_ERR_PARSE with *err_line otherwise) or packed words
+ * (n_packed x W, host), not both; FPS_ERR_BUDGET if the device copy would
+ * exceed hbm_budget_bytes (0 = no limit).
+ * fps_wide_search: query holds W words; writes min(k, N) results: out_index,
+ * and the measure as out_num / out_den (Manhattan: d / 1; Tanimoto: c / u,
+ * 0 / 0 for two empty sets).  Host memory and synchronous, or with
+ * FPS_SEARCH_DEVICE_IO device memory and asynchronous on cuda_stream.
+ */
+#define FPS_WIDE_MAX_BITS 2048
+#define FPS_METRIC_MANHATTAN 0
+#define FPS_METRIC_TANIMOTO 1
+typedef struct fps_wide_library_s* fps_wide_library;
+fps_status fps_wide_load(const char* text, size_t text_len, const uint64_t* packed, size_t n_packed, int n_bits,
+                         int device, size_t hbm_budget_bytes, fps_wide_library* out, size_t* err_line);
+fps_status fps_wide_info(fps_wide_library lib, int64_t* n_records, int* n_bits, size_t* device_bytes);
+fps_status fps_wide_search(fps_wide_library lib, const uint64_t* query, int k, int metric, int32_t* out_index,
+                           int32_t* out_num, int32_t* out_den, int32_t* out_count, uint32_t flags,
+                           void* cuda_stream);
+fps_status fps_wide_release(fps_wide_library lib);
+
 /* ----------------------------------------------------------------- helpers */
 
 const char* fps_status_string(fps_status st);

@@ -73,6 +73,11 @@ _lib.fps_search_batch.argtypes = [_vp, _vp, _i32, _vp, _vp, _vp, _vp, _vp, ctype
 _lib.fps_sync.argtypes = [_vp, _vp]
 _lib.fps_search_noalloc.argtypes = [_vp, _vp, _i32, _vp, _vp, _vp, _vp]
 _lib.fps_merge_topk.argtypes = [_vp, _vp, _vp, _i32, _i32, _vp, _vp, ctypes.POINTER(_i32)]
+_lib.fps_wide_load.argtypes = [_vp, ctypes.c_size_t, _vp, ctypes.c_size_t, _i32, _i32, ctypes.c_size_t,
+                               ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_size_t)]
+_lib.fps_wide_info.argtypes = [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_size_t)]
+_lib.fps_wide_search.argtypes = [_vp, _vp, _i32, _i32, _vp, _vp, _vp, _vp, ctypes.c_uint32, _vp]
+_lib.fps_wide_release.argtypes = [_vp]
 _lib.fps_search_shards.argtypes = [_vp, _i32, _vp, _vp, _i32, _vp, _vp, _vp, _vp, _vp,
                                    ctypes.POINTER(fps_search_opts), _vp, _vp]
 _lib.fps_batch_plan_create.argtypes = [_vp, _i32, _vp, _i32, _i32, ctypes.POINTER(_vp)]
@@ -93,7 +98,8 @@ for _f in ("fps_library_load", "fps_release", "fps_library_info_get", "fps_libra
            "fps_search_packed", "fps_search_batch", "fps_sync", "fps_pack_query", "fps_pack_text", "fps_search_noalloc",
            "fps_mlp_create", "fps_mlp_release", "fps_mlp_set_params", "fps_mlp_get_params", "fps_mlp_predict",
            "fps_mlp_grad", "fps_mlp_train_step", "fps_merge_topk", "fps_batch_plan_create", "fps_batch_plan_run",
-           "fps_batch_plan_release", "fps_search_shards"):
+           "fps_batch_plan_release", "fps_search_shards", "fps_wide_load", "fps_wide_info", "fps_wide_search",
+           "fps_wide_release"):
     getattr(_lib, _f).restype = _i32
 
 
@@ -522,3 +528,75 @@ def fps_batch_plan_release(plan: BatchPlan):
     if plan is not None and plan.handle:
         _check(_lib.fps_batch_plan_release(plan.handle), "fps_batch_plan_release")
         plan.handle = None
+
+
+# ------------------------------------------------------------------ wide
+FPS_WIDE_MAX_BITS, FPS_METRIC_MANHATTAN, FPS_METRIC_TANIMOTO = 2048, 0, 1
+
+
+class WideLibrary(Library):
+    """A resident library of n-bit fingerprints (owns its device memory until fps_wide_release)."""
+
+    def __init__(self, handle: int, n_bits: int):
+        super().__init__(handle)
+        self.n_bits = n_bits
+        self.words = (n_bits + 63) // 64
+
+    def __exit__(self, *exc):
+        fps_wide_release(self)
+
+
+def fps_wide_load(*, text=None, packed=None, n_bits: int, device: int = 0, hbm_budget_bytes: int = 0) -> WideLibrary:
+    """Load text (lines of n_bits '0'/'1' characters) or packed words (uint64 [N, W]) into device memory."""
+    h = _vp()
+    err = ctypes.c_size_t(0)
+    if text is not None:
+        buf = text if isinstance(text, (bytes, bytearray)) else bytes(text)
+        st = _lib.fps_wide_load(buf, len(buf), None, 0, int(n_bits), int(device), int(hbm_budget_bytes),
+                                ctypes.byref(h), ctypes.byref(err))
+    else:
+        # the library checks n_bits; a shape for the reshape even when it is out of range
+        pk = np.ascontiguousarray(np.asarray(packed, np.uint64).reshape(-1, max((int(n_bits) + 63) // 64, 1)))
+        st = _lib.fps_wide_load(None, 0, pk.ctypes.data, pk.shape[0], int(n_bits), int(device), int(hbm_budget_bytes),
+                                ctypes.byref(h), ctypes.byref(err))
+    _check(st, "fps_wide_load", err.value)
+    return WideLibrary(h.value, int(n_bits))
+
+
+def fps_wide_info(lib: WideLibrary) -> dict:
+    n, b, db = _i64(0), _i32(0), ctypes.c_size_t(0)
+    _check(_lib.fps_wide_info(lib._h, ctypes.byref(n), ctypes.byref(b), ctypes.byref(db)), "fps_wide_info")
+    return {"n_records": n.value, "n_bits": b.value, "device_bytes": db.value}
+
+
+def fps_wide_search(lib: WideLibrary, query, k: int, metric: int = FPS_METRIC_MANHATTAN, *, out_index=None,
+                    out_num=None, out_den=None, out_count=None, stream=None):
+    """Host form (NumPy query of W words): returns (index, num, den) with the measure num / den
+    (Manhattan d / 1, Tanimoto c / u).  Device form (CUDA tensor query): asynchronous on stream; returns
+    (out_index, out_num, out_den, out_count) CUDA int32 tensors."""
+    if _is_cuda(query):
+        import torch
+
+        dev = query.device
+        m = max(int(k), 1)
+        out_index = out_index if out_index is not None else torch.empty(m, dtype=torch.int32, device=dev)
+        out_num = out_num if out_num is not None else torch.empty(m, dtype=torch.int32, device=dev)
+        out_den = out_den if out_den is not None else torch.empty(m, dtype=torch.int32, device=dev)
+        out_count = out_count if out_count is not None else torch.empty(1, dtype=torch.int32, device=dev)
+        _check(_lib.fps_wide_search(lib._h, query.data_ptr(), int(k), int(metric), out_index.data_ptr(),
+                                    out_num.data_ptr(), out_den.data_ptr(), out_count.data_ptr(), FPS_SEARCH_DEVICE_IO,
+                                    _stream_ptr(stream)), "fps_wide_search")
+        return out_index, out_num, out_den, out_count
+    q = np.ascontiguousarray(np.asarray(query, np.uint64).reshape(lib.words))
+    m = max(int(k), 1)
+    idx, num, den, cnt = np.zeros(m, np.int32), np.zeros(m, np.int32), np.zeros(m, np.int32), np.zeros(1, np.int32)
+    _check(_lib.fps_wide_search(lib._h, q.ctypes.data, int(k), int(metric), idx.ctypes.data, num.ctypes.data,
+                                den.ctypes.data, cnt.ctypes.data, 0, _stream_ptr(stream)), "fps_wide_search")
+    c = int(cnt[0])
+    return idx[:c], num[:c], den[:c]
+
+
+def fps_wide_release(lib: WideLibrary):
+    if lib is not None and lib.handle:
+        _check(_lib.fps_wide_release(lib.handle), "fps_wide_release")
+        lib.handle = None

@@ -50,7 +50,7 @@ def parse_args():
     p.add_argument("--n", type=int, default=PAPER_N, help="library records")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--workload", default="single",
-                   choices=["single", "batch", "learned", "serve", "latency", "shards"],
+                   choices=["single", "batch", "learned", "serve", "latency", "shards", "wide"],
                    help="single: 16 sequential single queries per step (default); "
                         "batch: --queries queries with mixed k in one batched call per step")
     p.add_argument("--queries", type=int, default=4096)
@@ -823,6 +823,77 @@ def run_shards(args):
         fps.fps_release(lb)
 
 
+def run_wide(args):
+    """n-bit fingerprints (1024 and 2048 bits), Manhattan and Tanimoto: 16 sequential single queries."""
+    import torch
+
+    import oracle
+    import paper_1906_06170_gb300 as fps
+    import synth
+
+    torch.cuda.set_device(0)
+    n = args.n if args.n != PAPER_N else 20_000_000
+    peak, peak_kind = measured_peak_gbs()
+    stream = torch.cuda.current_stream()
+    results = {}
+    for n_bits in (1024, 2048):
+        packed = synth.wide_packed(n, n_bits, 0)
+        lib = fps.fps_wide_load(packed=packed, n_bits=n_bits)
+        del packed
+        W = synth.wide_words(n_bits)
+        qs = torch.from_numpy(synth.wide_packed(QUERIES_PER_STEP, n_bits, 1001).view(np.int64).copy()).cuda()
+        oi = torch.empty((QUERIES_PER_STEP, K), dtype=torch.int32, device="cuda")
+        on, od = torch.empty_like(oi), torch.empty_like(oi)
+        oc = torch.empty(QUERIES_PER_STEP, dtype=torch.int32, device="cuda")
+        for metric, name in ((fps.FPS_METRIC_MANHATTAN, "manhattan"), (fps.FPS_METRIC_TANIMOTO, "tanimoto")):
+            def step():
+                for j in range(QUERIES_PER_STEP):
+                    fps.fps_wide_search(lib, qs[j], K, metric, out_index=oi[j], out_num=on[j], out_den=od[j],
+                                        out_count=oc[j:j + 1], stream=stream)
+
+            for _ in range(args.warmup):
+                step()
+            torch.cuda.synchronize()
+            steps = max(args.steps // 10, 5)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(steps):
+                step()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b) / steps
+            assert np.all(oc.cpu().numpy() == min(K, n)), "wide results malformed"
+            per_q = ms / QUERIES_PER_STEP / 1e3
+            # every record's W words once per query (Tanimoto also reads its 2-byte popcount)
+            alg = 8.0 * W * n + (2.0 * n if metric == fps.FPS_METRIC_TANIMOTO else 0.0)
+            results[f"{n_bits}_{name}"] = {
+                "ms_per_step": ms, "value": QUERIES_PER_STEP * n / (ms / 1e3) / 1e9,
+                "roofline": {"bound": "hbm", "achieved": alg / per_q / 1e9, "peak": peak, "unit": "GB/s",
+                             "frac": alg / per_q / 1e9 / peak, "algorithmic_bytes_per_launch": alg,
+                             "traffic": None, "kernel": f"wide_scan_kernel<{name}>"}}
+        fps.fps_wide_release(lib)
+    # the oracle on a bounded sample (1024 bits, Tanimoto), for context
+    sample = 200_000
+    text = synth.wide_text(sample, 1024, 0)
+    q = synth.wide_to_strings(synth.wide_packed(1, 1024, 1001), 1024)[0]
+    t0 = time.perf_counter()
+    oracle.wide_topk(text, 1024, q, K, oracle.TANIMOTO)
+    dt = time.perf_counter() - t0
+    head = results["1024_tanimoto"]
+    line = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": 1, "steps": max(args.steps // 10, 5),
+            "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True, "dtype": "u64",
+            "data": "synthetic", "roofline": head["roofline"], "all": results,
+            "cpu_baseline": {"value": sample / dt / 1e9, "unit": UNIT, "cores": os.cpu_count() or 1, "kind": "oracle",
+                             "sample": f"1 Tanimoto query x {sample:,} 1024-bit records (parse + score + full sort), "
+                                       f"{dt:.2f} s"},
+            "config": {"workload": f"{n:,} generated n-bit fingerprints (seed 0, hashed-fingerprint density), "
+                                   f"{QUERIES_PER_STEP} sequential single queries per step (seed 1001), k={K}; "
+                                   "headline: 1024 bits, Tanimoto", "n_records": n, "k": K,
+                       "peak_source": peak_kind},
+            "gpu_launches": QUERIES_PER_STEP * max(args.steps // 10, 5)}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
@@ -831,6 +902,8 @@ def main():
         run_latency(args)
     elif args.workload == "shards":
         run_shards(args)
+    elif args.workload == "wide":
+        run_wide(args)
     elif args.workload == "batch":
         run_batch(args)
     elif args.workload == "learned":

@@ -18,12 +18,15 @@
 // and forms the key (one 64-bit division) only for records that pass.
 //
 // Layout in HBM: word-major tiles of 128 records, [tile][W][128] uint64, so a
-// warp reads 256 contiguous bytes per (word, 32 records).  One persistent
-// 8-warp block per SM; warps claim tiles one at a time from a counter (the
-// next claim issued while the current tile is scored), which lets faster SMs
-// take more tiles.  Each warp keeps the keys under its bound in a shared
-// buffer; when the buffer fills it sorts, keeps its best k and publishes the
-// k-th key as a global bound (atomicMin: k records at or under it exist).  The
+// warp reads 256 contiguous bytes per (word, 32 records); each lane keeps 32
+// loads (8 words of its 4 records) in flight.  One persistent block per SM
+// (16 warps for k <= 128, 8 with the larger buffers above); warps claim
+// 4-tile chunks from one counter (the next claim issued while the current
+// chunk is scored), which lets faster SMs take more tiles.  Each warp keeps
+// the keys under its bound in a shared buffer; when the buffer fills it sorts,
+// keeps its best k and publishes the k-th key as a global bound (atomicMin: k
+// records at or under it exist).  When its warps are done, every block sorts
+// their survivors, keeps its k best and publishes its own k-th key.  The
 // last block to finish gathers the survivors under the final bound, selects
 // the k smallest keys (bitonic sort in shared memory, or bisection over the key
 // when more survive than shared memory holds), recomputes c and u of the
@@ -46,11 +49,13 @@ namespace {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr int kWTile = 128;               // records per tile
-constexpr int kWarpsW = 8;                // warps per block
+constexpr int kClaimTiles = 4;            // tiles per claim from the tile counter
+constexpr int kWarpsMax = 16;             // warps per block, at most (16 for k <= 128, 8 above)
 constexpr int kMaxWords = FPS_WIDE_MAX_BITS / 64;
 
 struct WideLib {
   const uint64_t* words;  // [n_tiles][W][128]
+  const uint16_t* popc;   // [n_tiles * 128]: popc of each record (0 for padding)
   int64_t n;
   int64_t n_tiles;
   int W;
@@ -58,7 +63,7 @@ struct WideLib {
 
 struct WideState {
   unsigned long long thr_key;   // global bound on the k-th key
-  unsigned int ncand;           // survivors written by the warps
+  unsigned int ncand;           // unused (kept zero)
   unsigned int done;            // blocks finished
   unsigned int next_tile;       // tile counter
   unsigned int pad[3];
@@ -110,9 +115,9 @@ __device__ void block_sort(unsigned long long* s, int n) {
   }
 }
 
-// Keys the last block can sort in shared memory (the warp buffers' space, at least 8192 keys).
-__host__ __device__ constexpr int merge_cap(int cap_per_warp) {
-  return kWarpsW * cap_per_warp > 8192 ? kWarpsW * cap_per_warp : 8192;
+// Keys a block can sort in shared memory (the warp buffers' space, at least 8192 keys).
+__host__ __device__ constexpr int merge_cap(int warps, int cap_per_warp) {
+  return warps * cap_per_warp > 8192 ? warps * cap_per_warp : 8192;
 }
 
 __device__ __forceinline__ int pow2_at_least(int v) {
@@ -140,45 +145,67 @@ __device__ int compact_keys(unsigned long long* buf, int cnt, int k, unsigned lo
   return c;
 }
 
-template <int METRIC, int CAP>
-__global__ void __launch_bounds__(kWarpsW * 32, 1)
+template <int METRIC, int WARPS, int CAP>
+__global__ void __launch_bounds__(WARPS * 32, 1)
     wide_scan_kernel(WideLib L, const uint64_t* __restrict__ query, int k, WideState* st,
-                     unsigned long long* __restrict__ cand, int32_t* __restrict__ out_idx,
-                     int32_t* __restrict__ out_num, int32_t* __restrict__ out_den, int32_t* __restrict__ out_count) {
-  extern __shared__ __align__(16) unsigned long long wsm[];    // kWarpsW * CAP keys (reused by the merge)
+                     unsigned long long* __restrict__ cand, unsigned int* __restrict__ bcnt,
+                     int32_t* __restrict__ out_idx, int32_t* __restrict__ out_num, int32_t* __restrict__ out_den,
+                     int32_t* __restrict__ out_count) {
+  extern __shared__ __align__(16) unsigned long long wsm[];    // WARPS * CAP keys (reused by the merges)
   __shared__ uint64_t sq[kMaxWords];
-  __shared__ int s_last, s_cnt;
+  __shared__ int s_last, s_cnt, s_wcnt[WARPS];
   __shared__ unsigned long long s_lo, s_hi;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int W = L.W;
   for (int w = tid; w < W; w += blockDim.x) sq[w] = query[w];
   __syncthreads();
+  uint32_t pq = 0;   // popc of the query (Tanimoto: u = popc q + popc x - c)
+  for (int w = 0; w < W; ++w) pq += __popcll(sq[w]);
 
   unsigned long long* buf = wsm + static_cast<size_t>(warp) * CAP;
   int cnt = 0;
   unsigned long long thr = ld_relaxed_u64(&st->thr_key);
+  // tiles are claimed kClaimTiles at a time (one atomic per chunk on a single counter)
+  const int64_t n_chunks = (L.n_tiles + kClaimTiles - 1) / kClaimTiles;
   unsigned int next = 0;
   if (lane == 0) next = atomicAdd(&st->next_tile, 1u);
   next = __shfl_sync(kFull, next, 0);
-  while (next < static_cast<unsigned int>(L.n_tiles)) {
-    const int64_t t = next;
-    if (lane == 0) next = atomicAdd(&st->next_tile, 1u);   // the following tile, claimed while this one is scored
+  int sub = 0;
+  unsigned int chunk = next;
+  if (lane == 0 && chunk < n_chunks) next = atomicAdd(&st->next_tile, 1u);   // the following chunk
+  while (chunk < static_cast<unsigned int>(n_chunks)) {
+    const int64_t t = static_cast<int64_t>(chunk) * kClaimTiles + sub;
+    if (t >= L.n_tiles) break;
     const uint64_t* base = L.words + static_cast<size_t>(t) * W * kWTile;
     uint32_t a[4] = {0u, 0u, 0u, 0u}, b[4] = {0u, 0u, 0u, 0u};
-#pragma unroll 4
-    for (int w = 0; w < W; ++w) {
-      const uint64_t qw = sq[w];
-      const uint64_t* row = base + static_cast<size_t>(w) * kWTile + lane;
+    if (METRIC == FPS_METRIC_TANIMOTO) {
 #pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        const uint64_t x = __ldcs(row + 32 * m);
-        if (METRIC == FPS_METRIC_MANHATTAN) {
-          a[m] += __popcll(x ^ qw);
-        } else {
-          a[m] += __popcll(x & qw);
-          b[m] += __popcll(x | qw);
+      for (int m = 0; m < 4; ++m) b[m] = pq + __ldcs(L.popc + t * kWTile + lane + 32 * m);
+    }
+    // 8 words x 4 records = 32 streaming loads issued before any of them is used
+    for (int w0 = 0; w0 < W; w0 += 8) {
+      uint64_t x[8][4];
+#pragma unroll
+      for (int ww = 0; ww < 8; ++ww) {
+        const uint64_t* row = base + static_cast<size_t>(w0 + ww) * kWTile + lane;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) x[ww][m] = (w0 + ww < W) ? __ldcs(row + 32 * m) : 0ull;
+      }
+#pragma unroll
+      for (int ww = 0; ww < 8; ++ww) {
+        const uint64_t qw = (w0 + ww < W) ? sq[w0 + ww] : 0ull;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          if (METRIC == FPS_METRIC_MANHATTAN)
+            a[m] += __popcll(x[ww][m] ^ qw);
+          else
+            a[m] += __popcll(x[ww][m] & qw);
         }
       }
+    }
+    if (METRIC == FPS_METRIC_TANIMOTO) {
+#pragma unroll
+      for (int m = 0; m < 4; ++m) b[m] -= a[m];   // u = popc q + popc x - c
     }
     // the bound as a test without division: S <= S_b <=> c 2^24 >= (2^24 - S_b) u
     const uint32_t sb = static_cast<uint32_t>(thr >> 32);
@@ -209,15 +236,36 @@ __global__ void __launch_bounds__(kWarpsW * 32, 1)
     }
     const unsigned long long g = ld_relaxed_u64(&st->thr_key);
     thr = g < thr ? g : thr;
-    next = __shfl_sync(kFull, next, 0);
+    if (++sub == kClaimTiles) {
+      sub = 0;
+      chunk = __shfl_sync(kFull, next, 0);
+      if (lane == 0 && chunk < n_chunks) next = atomicAdd(&st->next_tile, 1u);
+    }
   }
   cnt = compact_keys<CAP>(buf, cnt, k, thr, lane);
   if (lane == 0 && cnt == k) atomicMin(&st->thr_key, thr);
+
+  // ---- block merge: the 8 warps' survivors -> the block's k best, its k-th key published as a
+  // bound; the block's slice of `cand` (8 FPS_K_MAX keys) is the staging area
+  unsigned long long* slice = cand + static_cast<size_t>(blockIdx.x) * kWarpsMax * FPS_K_MAX;
+  if (lane == 0) s_wcnt[warp] = cnt;
+  __syncthreads();
+  int off = 0, nb = 0;
+  for (int w2 = 0; w2 < WARPS; ++w2) {
+    off += w2 < warp ? s_wcnt[w2] : 0;
+    nb += s_wcnt[w2];
+  }
+  for (int i = lane; i < cnt; i += 32) slice[off + i] = buf[i];
+  __syncthreads();
   {
-    unsigned int at = 0;
-    if (lane == 0 && cnt > 0) at = atomicAdd(&st->ncand, static_cast<unsigned int>(cnt));
-    at = __shfl_sync(kFull, at, 0);
-    for (int i = lane; i < cnt; i += 32) cand[at + i] = buf[i];
+    const int p2 = pow2_at_least(nb > 1 ? nb : 1);
+    for (int i = tid; i < p2; i += blockDim.x) wsm[i] = i < nb ? slice[i] : ~0ull;
+    __syncthreads();
+    block_sort(wsm, p2);
+    const int kept = nb < k ? nb : k;
+    if (tid == 0 && kept == k) atomicMin(&st->thr_key, wsm[k - 1]);
+    for (int i = tid; i < kept; i += blockDim.x) slice[i] = wsm[i];
+    if (tid == 0) bcnt[blockIdx.x] = static_cast<unsigned int>(kept);
   }
 
   // ---- the last block selects the k smallest survivors
@@ -227,19 +275,22 @@ __global__ void __launch_bounds__(kWarpsW * 32, 1)
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  const int ncand = static_cast<int>(*reinterpret_cast<volatile unsigned int*>(&st->ncand));
   const int k_eff = static_cast<int>(k < L.n ? k : L.n);
-  const int cap = merge_cap(CAP);
+  const int cap = merge_cap(WARPS, CAP);
   unsigned long long* s = wsm;
   // only keys under the final bound can be among the k smallest (k keys at or under it exist)
   const unsigned long long fthr = ld_relaxed_u64(&st->thr_key);
+  auto survivor = [&](int b, int i) { return __ldcg(cand + static_cast<size_t>(b) * kWarpsMax * FPS_K_MAX + i); };
   if (tid == 0) s_cnt = 0;
   __syncthreads();
-  for (int i = tid; i < ncand; i += blockDim.x) {
-    const unsigned long long key = __ldcg(cand + i);
-    if (key <= fthr) {
-      const int p = atomicAdd(&s_cnt, 1);
-      if (p < cap) s[p] = key;
+  for (int b = 0; b < static_cast<int>(gridDim.x); ++b) {
+    const int nbk = static_cast<int>(*reinterpret_cast<volatile unsigned int*>(bcnt + b));
+    for (int i = tid; i < nbk; i += blockDim.x) {
+      const unsigned long long key = survivor(b, i);
+      if (key <= fthr) {
+        const int p = atomicAdd(&s_cnt, 1);
+        if (p < cap) s[p] = key;
+      }
     }
   }
   __syncthreads();
@@ -257,7 +308,10 @@ __global__ void __launch_bounds__(kWarpsW * 32, 1)
       if (tid == 0) s_cnt = 0;
       __syncthreads();
       int local = 0;
-      for (int i = tid; i < ncand; i += blockDim.x) local += __ldcg(cand + i) <= mid;
+      for (int b = 0; b < static_cast<int>(gridDim.x); ++b) {
+        const int nbk = static_cast<int>(bcnt[b]);
+        for (int i = tid; i < nbk; i += blockDim.x) local += survivor(b, i) <= mid;
+      }
       atomicAdd(&s_cnt, local);
       __syncthreads();
       if (tid == 0) {
@@ -271,11 +325,14 @@ __global__ void __launch_bounds__(kWarpsW * 32, 1)
     const unsigned long long K = s_lo;
     if (tid == 0) s_cnt = 0;
     __syncthreads();
-    for (int i = tid; i < ncand; i += blockDim.x) {
-      const unsigned long long key = __ldcg(cand + i);
-      if (key <= K) {
-        const int p = atomicAdd(&s_cnt, 1);
-        if (p < cap) s[p] = key;
+    for (int b = 0; b < static_cast<int>(gridDim.x); ++b) {
+      const int nbk = static_cast<int>(bcnt[b]);
+      for (int i = tid; i < nbk; i += blockDim.x) {
+        const unsigned long long key = survivor(b, i);
+        if (key <= K) {
+          const int p = atomicAdd(&s_cnt, 1);
+          if (p < cap) s[p] = key;
+        }
       }
     }
     __syncthreads();
@@ -324,18 +381,19 @@ __global__ void wide_state_init_kernel(WideState* st) {
   }
 }
 
-template <int METRIC, int CAP>
+template <int METRIC, int WARPS, int CAP>
 cudaError_t launch_wide(const WideLib& L, const uint64_t* q, int k, WideState* st, unsigned long long* cand,
-                        int32_t* oi, int32_t* on, int32_t* od, int32_t* oc, int num_sms, cudaStream_t s) {
-  auto kern = wide_scan_kernel<METRIC, CAP>;
-  const size_t smem = sizeof(unsigned long long) * merge_cap(CAP);
+                        unsigned int* bcnt, int32_t* oi, int32_t* on, int32_t* od, int32_t* oc, int num_sms,
+                        cudaStream_t s) {
+  auto kern = wide_scan_kernel<METRIC, WARPS, CAP>;
+  const size_t smem = sizeof(unsigned long long) * merge_cap(WARPS, CAP);
   static bool configured = false;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  kern<<<num_sms, kWarpsW * 32, smem, s>>>(L, q, k, st, cand, oi, on, od, oc);
+  kern<<<num_sms, WARPS * 32, smem, s>>>(L, q, k, st, cand, bcnt, oi, on, od, oc);
   return cudaGetLastError();
 }
 
@@ -344,7 +402,8 @@ constexpr int kSmallCapW = 256, kLargeCapW = 2048;
 // ------------------------------------------------------------------- host
 struct WideWs {
   WideState* st = nullptr;
-  unsigned long long* cand = nullptr;
+  unsigned long long* cand = nullptr;   // per block: 8 FPS_K_MAX keys
+  unsigned int* bcnt = nullptr;         // per block: survivors after the block merge
   uint64_t* q = nullptr;         // query (device)
   int32_t* out = nullptr;        // index, num, den (FPS_K_MAX each) + count (device)
   void* block = nullptr;
@@ -356,6 +415,7 @@ struct WideLibrary {
   int n_bits = 0;
   WideLib dev{};
   uint64_t* words = nullptr;
+  uint16_t* popc = nullptr;
   size_t device_bytes = 0;
   int num_sms = 0;
   std::mutex mu;
@@ -382,6 +442,7 @@ void free_wide(WideLibrary* L) {
     delete kv.second;
   }
   if (L->words) cudaFree(L->words);
+  if (L->popc) cudaFree(L->popc);
   delete L;
 }
 
@@ -394,9 +455,10 @@ fps_status wide_workspace(WideLibrary* L, cudaStream_t s, WideWs** out) {
   }
   WideWs* w = new (std::nothrow) WideWs();
   if (!w) return FPS_ERR_NOMEM;
-  const size_t cand_keys = static_cast<size_t>(L->num_sms) * kWarpsW * FPS_K_MAX;
+  const size_t cand_keys = static_cast<size_t>(L->num_sms) * kWarpsMax * FPS_K_MAX;
   const size_t st_b = 256, q_b = sizeof(uint64_t) * kMaxWords, out_b = sizeof(int32_t) * (3 * FPS_K_MAX + 1);
-  const size_t bytes = st_b + q_b + (out_b + 255) / 256 * 256 + cand_keys * sizeof(unsigned long long);
+  const size_t bytes = st_b + q_b + (out_b + 255) / 256 * 256 + cand_keys * sizeof(unsigned long long) +
+                       sizeof(unsigned int) * static_cast<size_t>(L->num_sms);
   if (cudaMalloc(&w->block, bytes) != cudaSuccess || cudaMallocHost(&w->host, out_b) != cudaSuccess) {
     cudaGetLastError();
     if (w->block) cudaFree(w->block);
@@ -408,6 +470,7 @@ fps_status wide_workspace(WideLibrary* L, cudaStream_t s, WideWs** out) {
   w->q = reinterpret_cast<uint64_t*>(b + st_b);
   w->out = reinterpret_cast<int32_t*>(b + st_b + q_b);
   w->cand = reinterpret_cast<unsigned long long*>(b + st_b + q_b + (out_b + 255) / 256 * 256);
+  w->bcnt = reinterpret_cast<unsigned int*>(w->cand + cand_keys);
   wide_state_init_kernel<<<1, 32, 0, s>>>(w->st);
   if (cudaGetLastError() != cudaSuccess) {
     cudaFree(w->block);
@@ -483,7 +546,8 @@ fps_status fps_wide_load(const char* text, size_t text_len, const uint64_t* pack
   if (n >= static_cast<int64_t>(INT32_MAX)) return FPS_ERR_UNSUPPORTED;
   const int64_t n_tiles = (n + kWTile - 1) / kWTile;
   const size_t bytes = static_cast<size_t>(n_tiles > 0 ? n_tiles : 1) * W * kWTile * sizeof(uint64_t);
-  if (hbm_budget_bytes && bytes > hbm_budget_bytes) return FPS_ERR_BUDGET;
+  const size_t pbytes = static_cast<size_t>(n_tiles > 0 ? n_tiles : 1) * kWTile * sizeof(uint16_t);
+  if (hbm_budget_bytes && bytes + pbytes > hbm_budget_bytes) return FPS_ERR_BUDGET;
   WideLibrary* L = new (std::nothrow) WideLibrary();
   if (!L) return FPS_ERR_NOMEM;
   L->device = device;
@@ -496,17 +560,25 @@ fps_status fps_wide_load(const char* text, size_t text_len, const uint64_t* pack
   }
   // word-major tiles: [tile][word][128 records], padding records zero
   std::vector<uint64_t> tiled(bytes / sizeof(uint64_t), 0ull);
-  for (int64_t r = 0; r < n; ++r)
-    for (int w = 0; w < W; ++w)
-      tiled[(static_cast<size_t>(r / kWTile) * W + w) * kWTile + (r % kWTile)] = src[static_cast<size_t>(r) * W + w];
-  if (cudaMalloc(&L->words, bytes) != cudaSuccess ||
-      cudaMemcpy(L->words, tiled.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+  std::vector<uint16_t> pc(pbytes / sizeof(uint16_t), 0);
+  for (int64_t r = 0; r < n; ++r) {
+    int p = 0;
+    for (int w = 0; w < W; ++w) {
+      const uint64_t x = src[static_cast<size_t>(r) * W + w];
+      tiled[(static_cast<size_t>(r / kWTile) * W + w) * kWTile + (r % kWTile)] = x;
+      p += __builtin_popcountll(x);
+    }
+    pc[static_cast<size_t>(r)] = static_cast<uint16_t>(p);
+  }
+  if (cudaMalloc(&L->words, bytes) != cudaSuccess || cudaMalloc(&L->popc, pbytes) != cudaSuccess ||
+      cudaMemcpy(L->words, tiled.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(L->popc, pc.data(), pbytes, cudaMemcpyHostToDevice) != cudaSuccess) {
     cudaGetLastError();
     free_wide(L);
     return FPS_ERR_CUDA;
   }
-  L->device_bytes = bytes;
-  L->dev = WideLib{L->words, n, n_tiles, W};
+  L->device_bytes = bytes + pbytes;
+  L->dev = WideLib{L->words, L->popc, n, n_tiles, W};
   *out = reinterpret_cast<fps_wide_library>(L);
   return FPS_OK;
 }
@@ -569,11 +641,11 @@ fps_status fps_wide_search(fps_wide_library lib, const uint64_t* query, int k, i
   cudaError_t e;
   const bool small = k <= kSmallCapW - kWTile;
   if (metric == FPS_METRIC_MANHATTAN)
-    e = small ? launch_wide<FPS_METRIC_MANHATTAN, kSmallCapW>(L->dev, dq, k, w->st, w->cand, oi, on, od, oc, L->num_sms, s)
-              : launch_wide<FPS_METRIC_MANHATTAN, kLargeCapW>(L->dev, dq, k, w->st, w->cand, oi, on, od, oc, L->num_sms, s);
+    e = small ? launch_wide<FPS_METRIC_MANHATTAN, 16, kSmallCapW>(L->dev, dq, k, w->st, w->cand, w->bcnt, oi, on, od, oc, L->num_sms, s)
+              : launch_wide<FPS_METRIC_MANHATTAN, 8, kLargeCapW>(L->dev, dq, k, w->st, w->cand, w->bcnt, oi, on, od, oc, L->num_sms, s);
   else
-    e = small ? launch_wide<FPS_METRIC_TANIMOTO, kSmallCapW>(L->dev, dq, k, w->st, w->cand, oi, on, od, oc, L->num_sms, s)
-              : launch_wide<FPS_METRIC_TANIMOTO, kLargeCapW>(L->dev, dq, k, w->st, w->cand, oi, on, od, oc, L->num_sms, s);
+    e = small ? launch_wide<FPS_METRIC_TANIMOTO, 16, kSmallCapW>(L->dev, dq, k, w->st, w->cand, w->bcnt, oi, on, od, oc, L->num_sms, s)
+              : launch_wide<FPS_METRIC_TANIMOTO, 8, kLargeCapW>(L->dev, dq, k, w->st, w->cand, w->bcnt, oi, on, od, oc, L->num_sms, s);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return FPS_ERR_CUDA;

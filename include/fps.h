@@ -334,6 +334,34 @@ fps_status fps_wide_search(fps_wide_library lib, const uint64_t* query, int k, i
                            void* cuda_stream);
 fps_status fps_wide_release(fps_wide_library lib);
 
+/*
+ * Batch clustering search (the paper's second search function, Sec. 4.4 and
+ * the results after Fig. 1: a batch of query molecules is clustered, the
+ * number of clusters chosen by the silhouette ("contour") coefficient, and
+ * the top molecules are listed per cluster).  The paper names no algorithm;
+ * this one (all integer, every tie to the smaller query index) is:
+ * k-medoids over the Manhattan distances between the Q queries, seeded with
+ * the most central query then farthest-first, alternating nearest-medoid
+ * assignment and medoid update (the member with the smallest sum of
+ * distances to its cluster) for at most 30 rounds; for every count c in
+ * [c_min, min(c_max, Q - 1)] the score is sum_i floor(s_i * 2^32) with s_i
+ * the silhouette of query i; the largest score (smaller c on ties) wins, and
+ * each of its clusters is searched with its medoid: the k nearest library
+ * records by (distance, index).  With Q - 1 < c_min there is one cluster
+ * around the most central query.
+ * Host memory, synchronous.  1 <= Q <= FPS_CLUSTER_MAX_Q; 2 <= c_min <= c_max
+ * <= FPS_CLUSTER_MAX_C; 0 <= k <= FPS_K_MAX.  Outputs: *out_c; out_labels[Q]
+ * (cluster of every query, 0 .. c-1); out_medoids[c] (query index of each
+ * cluster's medoid); out_scores[c_max - c_min + 1] (nullable; INT64_MIN for
+ * counts not tried); out_index / out_dist [c * k] and out_count[c]: cluster t's
+ * results at t * k.
+ */
+#define FPS_CLUSTER_MAX_Q 4096
+#define FPS_CLUSTER_MAX_C 16
+fps_status fps_cluster_search(fps_library lib, const uint64_t* queries, int Q, int c_min, int c_max, int k,
+                              int* out_c, int32_t* out_labels, int32_t* out_medoids, int64_t* out_scores,
+                              int32_t* out_index, int32_t* out_dist, int32_t* out_count, void* cuda_stream);
+
 /* ----------------------------------------------------------------- helpers */
 
 const char* fps_status_string(fps_status st);

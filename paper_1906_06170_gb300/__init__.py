@@ -78,6 +78,8 @@ _lib.fps_wide_load.argtypes = [_vp, ctypes.c_size_t, _vp, ctypes.c_size_t, _i32,
 _lib.fps_wide_info.argtypes = [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_size_t)]
 _lib.fps_wide_search.argtypes = [_vp, _vp, _i32, _i32, _vp, _vp, _vp, _vp, ctypes.c_uint32, _vp]
 _lib.fps_wide_release.argtypes = [_vp]
+_lib.fps_cluster_search.argtypes = [_vp, _vp, _i32, _i32, _i32, _i32, ctypes.POINTER(_i32), _vp, _vp, _vp, _vp, _vp,
+                                    _vp, _vp]
 _lib.fps_search_shards.argtypes = [_vp, _i32, _vp, _vp, _i32, _vp, _vp, _vp, _vp, _vp,
                                    ctypes.POINTER(fps_search_opts), _vp, _vp]
 _lib.fps_batch_plan_create.argtypes = [_vp, _i32, _vp, _i32, _i32, ctypes.POINTER(_vp)]
@@ -99,7 +101,7 @@ for _f in ("fps_library_load", "fps_release", "fps_library_info_get", "fps_libra
            "fps_mlp_create", "fps_mlp_release", "fps_mlp_set_params", "fps_mlp_get_params", "fps_mlp_predict",
            "fps_mlp_grad", "fps_mlp_train_step", "fps_merge_topk", "fps_batch_plan_create", "fps_batch_plan_run",
            "fps_batch_plan_release", "fps_search_shards", "fps_wide_load", "fps_wide_info", "fps_wide_search",
-           "fps_wide_release"):
+           "fps_wide_release", "fps_cluster_search"):
     getattr(_lib, _f).restype = _i32
 
 
@@ -600,3 +602,32 @@ def fps_wide_release(lib: WideLibrary):
     if lib is not None and lib.handle:
         _check(_lib.fps_wide_release(lib.handle), "fps_wide_release")
         lib.handle = None
+
+
+# ------------------------------------------------------------------ batch clustering
+FPS_CLUSTER_MAX_Q, FPS_CLUSTER_MAX_C = 4096, 16
+
+
+def fps_cluster_search(lib: Library, queries, k: int = 30, c_min: int = 2, c_max: int = 8, stream=None) -> dict:
+    """Batch clustering search (host arrays): cluster the packed queries [Q, 3] by k-medoids with the count
+    chosen by the silhouette, then the k nearest library records of every cluster's medoid.  Returns
+    {"c", "labels" [Q], "medoids" [c], "scores" {c: sum floor(s * 2^32)}, "results" [(index, distance)] * c}."""
+    q = np.ascontiguousarray(np.asarray(queries, np.uint64).reshape(-1, FPS_WORDS))
+    Q = q.shape[0]
+    n_c = max(int(c_max) - int(c_min) + 1, 1)
+    c = _i32(0)
+    labels = np.zeros(max(Q, 1), np.int32)
+    medoids = np.zeros(FPS_CLUSTER_MAX_C, np.int32)
+    scores = np.zeros(n_c, np.int64)
+    m = max(int(k), 1)
+    idx = np.zeros(FPS_CLUSTER_MAX_C * m, np.int32)
+    dist = np.zeros(FPS_CLUSTER_MAX_C * m, np.int32)
+    cnt = np.zeros(FPS_CLUSTER_MAX_C, np.int32)
+    _check(_lib.fps_cluster_search(lib._h, q.ctypes.data, Q, int(c_min), int(c_max), int(k), ctypes.byref(c),
+                                   labels.ctypes.data, medoids.ctypes.data, scores.ctypes.data, idx.ctypes.data,
+                                   dist.ctypes.data, cnt.ctypes.data, _stream_ptr(stream)), "fps_cluster_search")
+    cc = c.value
+    kk = int(k)
+    return {"c": cc, "labels": labels[:Q].copy(), "medoids": medoids[:cc].copy(),
+            "scores": {int(c_min) + i: int(v) for i, v in enumerate(scores) if v != np.iinfo(np.int64).min},
+            "results": [(idx[t * kk: t * kk + cnt[t]].copy(), dist[t * kk: t * kk + cnt[t]].copy()) for t in range(cc)]}

@@ -1311,6 +1311,148 @@ fps_status fps_search_shards(const fps_library* libs, int n_libs, const int64_t*
   return FPS_OK;
 }
 
+fps_status fps_cluster_search(fps_library lib, const uint64_t* queries, int Q, int c_min, int c_max, int k,
+                              int* out_c, int32_t* out_labels, int32_t* out_medoids, int64_t* out_scores,
+                              int32_t* out_index, int32_t* out_dist, int32_t* out_count, void* cuda_stream) {
+  if (!lib || !queries || Q < 1 || Q > FPS_CLUSTER_MAX_Q || c_min < 2 || c_max < c_min ||
+      c_max > FPS_CLUSTER_MAX_C || !out_c || !out_labels || !out_medoids || !out_count ||
+      (k > 0 && (!out_index || !out_dist)))
+    return FPS_ERR_INVALID_ARG;
+  fps_status st = check_k(k);
+  if (st != FPS_OK) return st;
+  for (int q = 0; q < Q; ++q)
+    if (queries[3 * q + 2] >> (kBits - 128)) return FPS_ERR_INVALID_ARG;
+  Library* L = reinterpret_cast<Library*>(lib);
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  DeviceGuard g(L->device);
+  if (!g.ok) return FPS_ERR_CUDA;
+  const int c_hi = std::min(c_max, Q - 1);
+  const int n_c = c_max - c_min + 1;
+  // device scratch: queries, D, row sums, near, cost, label per count, medoid per count, small words
+  Carve cv;
+  const size_t d_q = cv.take(sizeof(uint64_t) * 3 * Q);
+  const size_t d_D = cv.take(sizeof(int32_t) * static_cast<size_t>(Q) * Q);
+  const size_t d_rs = cv.take(sizeof(int32_t) * Q);
+  const size_t d_cost = cv.take(sizeof(int32_t) * Q);
+  const size_t d_lab = cv.take(sizeof(int32_t) * static_cast<size_t>(Q) * n_c);
+  const size_t d_seed = cv.take(sizeof(int32_t) * kClusterMaxC);
+  const size_t d_med = cv.take(sizeof(int32_t) * kClusterMaxC * n_c);
+  const size_t d_tmp = cv.take(sizeof(int32_t) * kClusterMaxC);
+  const size_t d_flag = cv.take(sizeof(int32_t) * 2);
+  const size_t d_sizes = cv.take(sizeof(int32_t) * kClusterMaxC);
+  const size_t d_score = cv.take(sizeof(unsigned long long) * n_c);
+  char* db = nullptr;
+  int32_t* hflag = nullptr;
+  if (cudaMalloc(&db, cv.at) != cudaSuccess || cudaMallocHost(&hflag, sizeof(int32_t) * 2) != cudaSuccess) {
+    cudaGetLastError();
+    if (db) cudaFree(db);
+    return FPS_ERR_CUDA;
+  }
+  auto fail = [&](fps_status code) {
+    cudaGetLastError();
+    cudaStreamSynchronize(s);
+    cudaFree(db);
+    cudaFreeHost(hflag);
+    return code;
+  };
+  int32_t* D = reinterpret_cast<int32_t*>(db + d_D);
+  int32_t* rs = reinterpret_cast<int32_t*>(db + d_rs);
+  int32_t* cost = reinterpret_cast<int32_t*>(db + d_cost);
+  int32_t* seed = reinterpret_cast<int32_t*>(db + d_seed);
+  int32_t* tmp = reinterpret_cast<int32_t*>(db + d_tmp);
+  int32_t* flag = reinterpret_cast<int32_t*>(db + d_flag);
+  int32_t* sizes = reinterpret_cast<int32_t*>(db + d_sizes);
+  unsigned long long* score = reinterpret_cast<unsigned long long*>(db + d_score);
+  if (cudaMemcpyAsync(db + d_q, queries, sizeof(uint64_t) * 3 * Q, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemsetAsync(score, 0, sizeof(unsigned long long) * n_c, s) != cudaSuccess ||
+      cluster_qdist(reinterpret_cast<const uint64_t*>(db + d_q), Q, D, s) != cudaSuccess ||
+      cluster_rowsum(D, Q, nullptr, rs, s) != cudaSuccess ||
+      cluster_select(rs, Q, false, nullptr, 0, nullptr, 0, seed, s) != cudaSuccess)
+    return fail(FPS_ERR_CUDA);
+  // farthest-first seeds up to the largest count (the seeds of a count are a prefix of them);
+  // rs serves as the distance to the nearest seed
+  for (int t = 1; t < c_hi; ++t) {
+    if (cluster_near(D, Q, seed + t - 1, t == 1, rs, s) != cudaSuccess ||
+        cluster_select(rs, Q, true, seed, t, nullptr, 0, seed + t, s) != cudaSuccess)
+      return fail(FPS_ERR_CUDA);
+  }
+  for (int c = c_min; c <= c_hi; ++c) {
+    const int slot = c - c_min;
+    int32_t* med = reinterpret_cast<int32_t*>(db + d_med) + kClusterMaxC * slot;
+    int32_t* lab = reinterpret_cast<int32_t*>(db + d_lab) + static_cast<size_t>(Q) * slot;
+    if (cudaMemcpyAsync(med, seed, sizeof(int32_t) * c, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      return fail(FPS_ERR_CUDA);
+    for (int it = 0; it < kClusterIters; ++it) {
+      if (cluster_assign(D, Q, med, c, lab, s) != cudaSuccess || cluster_rowsum(D, Q, lab, cost, s) != cudaSuccess ||
+          cluster_medoids(cost, lab, Q, c, med, tmp, flag, s) != cudaSuccess ||
+          cudaMemcpyAsync(hflag, flag, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+          cudaStreamSynchronize(s) != cudaSuccess)
+        return fail(FPS_ERR_CUDA);
+      if (!hflag[0]) break;   // the medoids repeat: lab already belongs to them
+      if (cudaMemcpyAsync(med, tmp, sizeof(int32_t) * c, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return fail(FPS_ERR_CUDA);
+      if (it + 1 == kClusterIters && cluster_assign(D, Q, med, c, lab, s) != cudaSuccess)
+        return fail(FPS_ERR_CUDA);
+    }
+    if (cluster_silhouette(D, Q, lab, c, sizes, score + slot, s) != cudaSuccess) return fail(FPS_ERR_CUDA);
+  }
+  std::vector<unsigned long long> sc(n_c, 0ull);
+  if (cudaMemcpyAsync(sc.data(), score, sizeof(unsigned long long) * n_c, cudaMemcpyDeviceToHost, s) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return fail(FPS_ERR_CUDA);
+  int best = 1;
+  long long best_score = 0;
+  for (int c = c_min; c <= c_hi; ++c) {
+    const long long v = static_cast<long long>(sc[c - c_min]);
+    if (best == 1 || v > best_score) {
+      best = c;
+      best_score = v;
+    }
+  }
+  if (out_scores)
+    for (int c = c_min; c <= c_max; ++c)
+      out_scores[c - c_min] = c <= c_hi ? static_cast<int64_t>(sc[c - c_min]) : INT64_MIN;
+  std::vector<int32_t> med_h(kClusterMaxC, 0);
+  if (best == 1) {   // fewer than c_min + 1 queries: one cluster around the most central query
+    if (cudaMemcpyAsync(med_h.data(), seed, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return fail(FPS_ERR_CUDA);
+    for (int q = 0; q < Q; ++q) out_labels[q] = 0;
+  } else {
+    const int slot = best - c_min;
+    if (cudaMemcpyAsync(med_h.data(), reinterpret_cast<int32_t*>(db + d_med) + kClusterMaxC * slot,
+                        sizeof(int32_t) * best, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(out_labels, reinterpret_cast<int32_t*>(db + d_lab) + static_cast<size_t>(Q) * slot,
+                        sizeof(int32_t) * Q, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return fail(FPS_ERR_CUDA);
+  }
+  cudaFree(db);
+  cudaFreeHost(hflag);
+  *out_c = best;
+  for (int t = 0; t < best; ++t) out_medoids[t] = med_h[t];
+  // every cluster searched with its medoid (one after another through the single-query scan)
+  std::vector<uint64_t> mq(3 * static_cast<size_t>(best));
+  std::vector<int32_t> kk(best, k);
+  std::vector<int64_t> off(best + 1, 0);
+  for (int t = 0; t < best; ++t) {
+    std::memcpy(&mq[3 * t], queries + 3 * static_cast<size_t>(med_h[t]), 3 * sizeof(uint64_t));
+    off[t + 1] = off[t] + k;
+  }
+  fps_search_opts o{};
+  o.path = FPS_PATH_POPC;
+  std::vector<int32_t> ti(std::max<int64_t>(off[best], 1)), td(std::max<int64_t>(off[best], 1));
+  st = search_batch_impl(L, mq.data(), best, kk.data(), off.data(), off[best], ti.data(), td.data(), out_count, &o,
+                         false, s);
+  if (st != FPS_OK) return st;
+  for (int t = 0; t < best && k > 0; ++t) {
+    std::memcpy(out_index + static_cast<size_t>(t) * k, ti.data() + off[t], sizeof(int32_t) * out_count[t]);
+    std::memcpy(out_dist + static_cast<size_t>(t) * k, td.data() + off[t], sizeof(int32_t) * out_count[t]);
+  }
+  return FPS_OK;
+}
+
 fps_status fps_merge_topk(const int32_t* idx, const int32_t* dist, const int64_t* part_off, int parts, int k,
                           int32_t* out_index, int32_t* out_dist, int* out_n) {
   if (parts < 0 || k < 0 || !part_off || !out_n || (k > 0 && (!out_index || !out_dist))) return FPS_ERR_INVALID_ARG;

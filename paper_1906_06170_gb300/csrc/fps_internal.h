@@ -154,6 +154,23 @@ cudaError_t launch_shard_merge(const ShardLists& sl, int Q, const int64_t* off, 
 // *slot_dev = value, in stream order (slot_dev: device view of pinned host memory)
 cudaError_t launch_progress(int64_t* slot_dev, int64_t value, cudaStream_t s);
 
+// ---- batch clustering (fps_cluster.cu); every tie goes to the smaller query index
+constexpr int kClusterMaxC = 16;    // largest cluster count
+constexpr int kClusterIters = 30;   // k-medoids rounds at most
+cudaError_t cluster_qdist(const uint64_t* q, int Q, int32_t* D, cudaStream_t s);            // Q x Q distances
+// out[i] = sum_j D[i][j] (lab == nullptr) or the sum over i's own cluster
+cudaError_t cluster_rowsum(const int32_t* D, int Q, const int32_t* lab, int32_t* out, cudaStream_t s);
+cudaError_t cluster_near(const int32_t* D, int Q, const int32_t* m, bool first, int32_t* near, cudaStream_t s);
+// *out = argmin (or argmax) of val over the queries not in ex[0..n_ex) (lab == nullptr) or with lab == want
+cudaError_t cluster_select(const int32_t* val, int Q, bool largest, const int32_t* ex, int n_ex, const int32_t* lab,
+                           int want, int32_t* out, cudaStream_t s);
+cudaError_t cluster_assign(const int32_t* D, int Q, const int32_t* med, int c, int32_t* lab, cudaStream_t s);
+cudaError_t cluster_medoids(const int32_t* cost, const int32_t* lab, int Q, int c, const int32_t* med_old,
+                            int32_t* med_new, int32_t* changed, cudaStream_t s);
+// *score += sum_i floor(s_i 2^32) (two's complement in 64 bits)
+cudaError_t cluster_silhouette(const int32_t* D, int Q, const int32_t* lab, int c, int32_t* sizes,
+                               unsigned long long* score, cudaStream_t s);
+
 // ---- tensor-core batched scan (fps_tc.cu)
 size_t tc_operand_bytes(int64_t n_tiles128);
 size_t tc_query_operand_bytes(int Q);

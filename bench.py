@@ -50,7 +50,7 @@ def parse_args():
     p.add_argument("--n", type=int, default=PAPER_N, help="library records")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--workload", default="single",
-                   choices=["single", "batch", "learned", "serve", "latency", "shards", "wide"],
+                   choices=["single", "batch", "learned", "serve", "latency", "shards", "wide", "cluster"],
                    help="single: 16 sequential single queries per step (default); "
                         "batch: --queries queries with mixed k in one batched call per step")
     p.add_argument("--queries", type=int, default=4096)
@@ -894,6 +894,57 @@ def run_wide(args):
     print(json.dumps(line), flush=True)
 
 
+def run_cluster(args):
+    """Batch clustering search: 4096 queries around 8 library molecules (near-duplicates of them), clustered
+    by k-medoids with the count from the silhouette (2..16), each cluster searched with its medoid."""
+    import torch
+
+    import paper_1906_06170_gb300 as fps
+    import synth
+    from oracle import cluster
+
+    torch.cuda.set_device(0)
+    n = args.n
+    lib = fps.fps_library_load(packed=synth.packed(n, 0))
+    Q, groups = args.queries, 8
+    centers = synth.packed_at([synth.draw(9, g, 1) % n for g in range(groups)], 0)
+    qs = np.repeat(centers, Q // groups, axis=0)
+    for i in range(qs.shape[0]):                      # 0-6 seeded flips per query
+        for t in range(synth.draw(9, 1000 + i, 1) % 7):
+            j = 1 + synth.draw(9, 1000 + i, 2 + t) % 165
+            qs[i, j // 64] ^= np.uint64(1) << np.uint64(j % 64)
+    for _ in range(args.warmup):
+        res = fps.fps_cluster_search(lib, qs, k=K, c_min=2, c_max=16)
+    steps = max(args.steps // 40, 3)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        res = fps.fps_cluster_search(lib, qs, k=K, c_min=2, c_max=16)
+    ms = (time.perf_counter() - t0) / steps * 1e3
+    # the clustering alone: the same call with k = 0 (no library search)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        fps.fps_cluster_search(lib, qs, k=0, c_min=2, c_max=16)
+    ms_cluster = (time.perf_counter() - t0) / steps * 1e3
+    # the oracle on a bounded sample of the batch (its distance matrix is Q x Q x 166 booleans)
+    sample = 512
+    sq = synth.packed_to_strings(qs[:: Q // sample][:sample])
+    t0 = time.perf_counter()
+    cluster.cluster_batch(sq, 2, 16)
+    cpu_s = time.perf_counter() - t0
+    line = {"metric": "batch clustering search: batches/s, exact", "value": 1e3 / ms, "unit": "batches/s",
+            "n_gpus": 1, "steps": steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "data": "synthetic", "chosen_clusters": res["c"], "ms_clustering": ms_cluster,
+            "ms_searches": ms - ms_cluster,
+            "cpu_baseline": {"value": 1.0 / cpu_s, "unit": "batches/s", "cores": 1, "kind": "oracle",
+                             "sample": f"clustering of {sample} of the {Q} queries (counts 2..16), {cpu_s:.2f} s"},
+            "config": {"workload": f"{Q} queries: {groups} library records (seed 0) with 0-6 seeded bit flips each; "
+                                   f"counts 2..16 by silhouette; each cluster's medoid searched over {n:,} records, "
+                                   f"k={K}; host buffers, synchronous call", "n_records": n, "queries": Q}}
+    print(json.dumps(line), flush=True)
+    fps.fps_release(lib)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
@@ -904,6 +955,8 @@ def main():
         run_shards(args)
     elif args.workload == "wide":
         run_wide(args)
+    elif args.workload == "cluster":
+        run_cluster(args)
     elif args.workload == "batch":
         run_batch(args)
     elif args.workload == "learned":

@@ -50,6 +50,7 @@ namespace {
 constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr int kWTile = 128;               // records per tile
 constexpr int kClaimTiles = 4;            // tiles per claim from the tile counter
+constexpr int kMaxBlocks = 1024;          // grid size limit (one block per SM)
 constexpr int kWarpsMax = 16;             // warps per block, at most (16 for k <= 128, 8 above)
 constexpr int kMaxWords = FPS_WIDE_MAX_BITS / 64;
 
@@ -154,6 +155,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
   extern __shared__ __align__(16) unsigned long long wsm[];    // WARPS * CAP keys (reused by the merges)
   __shared__ uint64_t sq[kMaxWords];
   __shared__ int s_last, s_cnt, s_wcnt[WARPS];
+  __shared__ int s_bcnt[kMaxBlocks];
   __shared__ unsigned long long s_lo, s_hi;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int W = L.W;
@@ -281,16 +283,20 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
   // only keys under the final bound can be among the k smallest (k keys at or under it exist)
   const unsigned long long fthr = ld_relaxed_u64(&st->thr_key);
   auto survivor = [&](int b, int i) { return __ldcg(cand + static_cast<size_t>(b) * kWarpsMax * FPS_K_MAX + i); };
+  // every block's count at once (a loop over blocks with a dependent load each would serialise
+  // gridDim.x memory round trips), then one flattened pass over (block, slot)
+  for (int b = tid; b < static_cast<int>(gridDim.x); b += blockDim.x)
+    s_bcnt[b] = static_cast<int>(*reinterpret_cast<volatile unsigned int*>(bcnt + b));
   if (tid == 0) s_cnt = 0;
   __syncthreads();
-  for (int b = 0; b < static_cast<int>(gridDim.x); ++b) {
-    const int nbk = static_cast<int>(*reinterpret_cast<volatile unsigned int*>(bcnt + b));
-    for (int i = tid; i < nbk; i += blockDim.x) {
-      const unsigned long long key = survivor(b, i);
-      if (key <= fthr) {
-        const int p = atomicAdd(&s_cnt, 1);
-        if (p < cap) s[p] = key;
-      }
+  const int slots = static_cast<int>(gridDim.x) * k;   // a block keeps at most k keys
+  for (int x = tid; x < slots; x += blockDim.x) {
+    const int b = x / k, i = x - b * k;
+    if (i >= s_bcnt[b]) continue;
+    const unsigned long long key = survivor(b, i);
+    if (key <= fthr) {
+      const int p = atomicAdd(&s_cnt, 1);
+      if (p < cap) s[p] = key;
     }
   }
   __syncthreads();
@@ -308,9 +314,9 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
       if (tid == 0) s_cnt = 0;
       __syncthreads();
       int local = 0;
-      for (int b = 0; b < static_cast<int>(gridDim.x); ++b) {
-        const int nbk = static_cast<int>(bcnt[b]);
-        for (int i = tid; i < nbk; i += blockDim.x) local += survivor(b, i) <= mid;
+      for (int x = tid; x < slots; x += blockDim.x) {
+        const int b = x / k, i = x - b * k;
+        if (i < s_bcnt[b]) local += survivor(b, i) <= mid;
       }
       atomicAdd(&s_cnt, local);
       __syncthreads();
@@ -325,14 +331,13 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
     const unsigned long long K = s_lo;
     if (tid == 0) s_cnt = 0;
     __syncthreads();
-    for (int b = 0; b < static_cast<int>(gridDim.x); ++b) {
-      const int nbk = static_cast<int>(bcnt[b]);
-      for (int i = tid; i < nbk; i += blockDim.x) {
-        const unsigned long long key = survivor(b, i);
-        if (key <= K) {
-          const int p = atomicAdd(&s_cnt, 1);
-          if (p < cap) s[p] = key;
-        }
+    for (int x = tid; x < slots; x += blockDim.x) {
+      const int b = x / k, i = x - b * k;
+      if (i >= s_bcnt[b]) continue;
+      const unsigned long long key = survivor(b, i);
+      if (key <= K) {
+        const int p = atomicAdd(&s_cnt, 1);
+        if (p < cap) s[p] = key;
       }
     }
     __syncthreads();
@@ -393,6 +398,7 @@ cudaError_t launch_wide(const WideLib& L, const uint64_t* q, int k, WideState* s
     if (e != cudaSuccess) return e;
     configured = true;
   }
+  if (num_sms > kMaxBlocks) return cudaErrorInvalidConfiguration;
   kern<<<num_sms, WARPS * 32, smem, s>>>(L, q, k, st, cand, bcnt, oi, on, od, oc);
   return cudaGetLastError();
 }

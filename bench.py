@@ -175,18 +175,23 @@ def cpu_oracle_throughput(records: int, nq: int, seconds_hint: str):
     for q in qs:
         oracle.topk(text, q, K, threads=threads)
     dt = time.perf_counter() - t0
-    # the distance step alone (parse + character compares, all threads) on two of the queries;
-    # the rest of a query's time is the full sort of its N (distance, index) pairs
+    # split of one query: parse (oracle.count parses only), parse + distances (oracle.distances
+    # parses twice: once to count, once to score), parse + distances + full sort (oracle.topk)
     nd = min(2, nq)
+    t1 = time.perf_counter()
+    for _ in range(nd):
+        oracle.count(text)
+    parse_s = (time.perf_counter() - t1) / nd
     t1 = time.perf_counter()
     for q in qs[:nd]:
         oracle.distances(text, q, threads=threads)
-    dist_s = (time.perf_counter() - t1) / nd
+    dist_s = max((time.perf_counter() - t1) / nd - 2 * parse_s, 0.0)
     per_q = dt / nq
     return {"value": records * nq / dt / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"{nq} queries x {records:,} records of the same generator (parse + distances on "
                       f"{threads} threads + full sort), {dt:.1f} s{seconds_hint}",
-            "split_s_per_query": {"distances": dist_s, "sort": max(per_q - dist_s, 0.0)},
+            "split_s_per_query": {"parse": parse_s, "distances": dist_s,
+                                  "sort": max(per_q - parse_s - dist_s, 0.0)},
             "paper_method_context": paper_method_context()}
 
 

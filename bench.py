@@ -121,6 +121,7 @@ class ClockSampler:
 # one 166-bit comparison costs 6 (three 64-bit popcounts), so the popcount paths' ALU bound is
 # 16 / 6 comparisons per SM per clock.
 POPC32_PER_SM_CLK = 16.0
+SPIN_CYCLES = 200_000          # ~0.1 ms of GPU spin ahead of a latency sample
 POPC32_PER_COMPARISON = 6.0
 SMS, SM_MAX_MHZ = 152, 2070.0
 
@@ -375,7 +376,9 @@ def run_gb300(args):
 def run_latency(args):
     """Single query over a 1,000,000-record library (24 MB, inside the 129 MB L2): warm latency (library
     cached in L2 by the previous query), cold latency (a 512 MB scratch buffer written before each query
-    evicts it), and end-to-end latency through the C ABI with host buffers."""
+    evicts it), and end-to-end latency through the C ABI with host buffers.  Device latencies are taken
+    with the GPU kept busy (a spin kernel) while the host enqueues the search, so that the events bracket
+    the search alone; the call latency beside them leaves the GPU idle until the launch arrives."""
     import torch
 
     import paper_1906_06170_gb300 as fps
@@ -396,11 +399,13 @@ def run_latency(args):
     def one():
         fps.fps_search_packed(lib, qd[0], K, out_index=oi, out_dist=od, out_count=oc, stream=stream)
 
-    def timed(cold, reps):
+    def timed(cold, reps, busy=True):
         ts = []
         for i in range(reps):
             if cold:
                 scratch.fill_(i & 0xFF)
+            if busy:
+                torch.cuda._sleep(SPIN_CYCLES)
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             a.record(stream)
@@ -418,6 +423,7 @@ def run_latency(args):
     reps = max(args.steps, 20)
     warm = timed(False, reps)
     cold = timed(True, max(reps // 4, 10))
+    call = timed(False, max(reps // 4, 10), busy=False)
     clk = clocks.stop()
     qh = q[0].copy()
     e2e = []
@@ -439,7 +445,12 @@ def run_latency(args):
             "dtype": "u64", "data": "synthetic",
             "latency_us": {"warm_p50": p50w, "warm_p99": float(np.percentile(warm, 99)),
                            "cold_p50": p50c, "cold_p99": float(np.percentile(cold, 99)),
-                           "e2e_host_p50": float(np.median(e2e)), "e2e_host_p99": float(np.percentile(e2e, 99))},
+                           "call_p50": float(np.median(call)),
+                       "e2e_host_p50": float(np.median(e2e)), "e2e_host_p99": float(np.percentile(e2e, 99))},
+            "latency_note": "warm/cold: device time of the search (events on the launching stream, GPU busy "
+                            "while the host enqueues it); call: the same with the GPU idle until the launch "
+                            "arrives (adds the host's launch time); e2e_host: host buffers through the C ABI, "
+                            "wall clock",
             "cold_value": n / (p50c * 1e-6) / 1e9,
             "roofline_cold": {"bound": "hbm", "achieved": alg / (p50c * 1e-6) / 1e9, "peak": peak, "unit": "GB/s",
                               "frac": alg / (p50c * 1e-6) / 1e9 / peak, "algorithmic_bytes_per_launch": alg,

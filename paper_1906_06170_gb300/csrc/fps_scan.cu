@@ -16,10 +16,13 @@
 //     as the bound of its next tile exceeds the current distance threshold;
 //   * a record is a candidate iff its key is <= the running threshold key.
 //     The threshold is the min of (a) the smallest D such that at least k
-//     accepted records have d <= D, read from a global histogram of accepted
-//     distances, and (b) the k-th key of any warp's local buffer (atomicMin).
+//     accepted records have d <= D, read from the block's own histogram of
+//     accepted distances in shared memory and published to all blocks
+//     (atomicMin), and (b) the k-th key of any warp's local buffer (atomicMin).
 //     Both are valid upper bounds of the true k-th key, so no top-k member is
-//     ever rejected;
+//     ever rejected.  The block histograms reach the global one once, when
+//     their block ends: a global histogram updated and re-read after every
+//     tile puts every warp of the grid on the same few L2 lines;
 //   * candidates go to a per-warp shared buffer; a full buffer is filtered
 //     against the threshold and, if still longer than k, sorted and cut to k;
 //   * the last CTA to finish reads the histogram -- exact below the final
@@ -223,18 +226,16 @@ __device__ int compact_buffer(unsigned long long* buf, int cnt, int k, unsigned 
   return kept;
 }
 
-// The smallest D with at least k accepted records at distance <= D; 167 if none.
-// Lane l reads bins 6l .. 6l+5 in one round trip (L2, bypassing L1).
-__device__ uint32_t bound_from_hist(const ScanState* st, int k, int lane) {
+// The smallest D with at least k accepted records at distance <= D in the
+// block's histogram; 167 if none.  Lane l reads bins 6l .. 6l+5.  Other warps
+// of the block may be adding to it: counts only grow, so a stale read gives a
+// looser bound, never an invalid one (k distinct records within D exist).
+__device__ uint32_t bound_from_block_hist(const uint32_t* sh_hist, int k, int lane) {
   uint32_t h[6] = {0, 0, 0, 0, 0, 0};
   if (lane < 28) {
-    const uint2* p = reinterpret_cast<const uint2*>(st->hist + 6 * lane);
+    const volatile uint32_t* p = sh_hist + 6 * lane;
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      uint2 v = __ldcg(p + i);
-      h[2 * i] = v.x;
-      h[2 * i + 1] = v.y;
-    }
+    for (int i = 0; i < 6; ++i) h[i] = p[i];
   }
   uint32_t sum = h[0] + h[1] + h[2] + h[3] + h[4] + h[5];
   uint32_t incl = sum;
@@ -257,12 +258,11 @@ __device__ uint32_t bound_from_hist(const ScanState* st, int k, int lane) {
   return __shfl_sync(kFull, found, src);
 }
 
-// Move the block's pending histogram counts to the global histogram.  The
-// exchange makes each count leave shared memory exactly once, whichever warps
-// flush concurrently.
-__device__ __forceinline__ void flush_hist(uint32_t* sh_hist, ScanState* st, int lane) {
+// Add the block's histogram to the global one (one warp, after the block's
+// scan has ended).
+__device__ __forceinline__ void flush_hist(const uint32_t* sh_hist, ScanState* st, int lane) {
   for (int b = lane; b < kNumBuckets; b += 32) {
-    uint32_t v = atomicExch(&sh_hist[b], 0u);
+    const uint32_t v = sh_hist[b];
     if (v) red_add_u32(&st->hist[b], v);
   }
   __syncwarp();
@@ -278,7 +278,7 @@ __device__ __forceinline__ void count_accepted(uint32_t* sh_hist, bool acc, uint
 }
 
 struct Tables {
-  uint32_t sh_hist[168];          // accepted records per distance, not yet added to the global histogram
+  uint32_t sh_hist[168];          // accepted records of this block per distance
   int lv_start[kNumBuckets + 2];  // items before level L (level = |popc q - bucket|)
   int lo_b[kNumBuckets + 1];      // bucket popc q - L, or -1
   int hi_b[kNumBuckets + 1];      // bucket popc q + L, or -1
@@ -291,6 +291,8 @@ struct Tables {
   int ntie;
   int T;
   int cless;
+  int wbase[32];                  // first candidate slot of each warp of the block
+  uint32_t blk_base;              // first candidate slot of the block
 };
 
 struct Item {
@@ -328,6 +330,7 @@ struct Smem {
   static constexpr size_t items = static_cast<size_t>(WARPS) * kStages * 4;
   static constexpr size_t total = ring + bufs + bars + items + sizeof(Tables);
   static_assert(ring + bufs >= (kFinCap + kTieCap) * 8, "merge scratch must fit in the scan buffers");
+  static_assert(WARPS <= 32, "one candidate base per warp in the tables");
 };
 
 // ---------------------------------------------------------------------- kernel
@@ -528,70 +531,49 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
         c[m] = (r < it.nvalid) && (d[m] <= D);
         any |= c[m];
       }
-      if (j == 0 && k < kTile) {
-        // First tile of the warp: keep only its own k best records.  A tile lies
-        // inside one popcount bucket, where position order is index order, so
-        // sorting (d, position) orders exactly like (d, index).  Dropped records
-        // are worse than k records of this tile, hence never in the top k.
-        if (__any_sync(kFull, any)) {
-#pragma unroll
-          for (int m = 0; m < 4; ++m)
-            buf[lane + 32 * m] = c[m] ? ((static_cast<unsigned long long>(d[m]) << 32) | (lane + 32 * m)) : ~0ull;
+      if (__any_sync(kFull, any)) {
+        // Re-derive the bound from the block's histogram and publish it.
+        auto refresh_bound = [&]() {
           __syncwarp();
-          warp_bitonic_sort(buf, kTile, lane);
-          int kept = 0;
-          for (int base = 0; base < k; base += 32) {
-            int i = base + lane;
-            unsigned long long e = i < k ? buf[i] : ~0ull;
-            bool acc = e != ~0ull;
-            uint32_t dd = static_cast<uint32_t>(e >> 32);
-            uint32_t bal = __ballot_sync(kFull, acc);
-            if (acc) {
-              int32_t idx = __ldg(lib.perm + it.tile * kTile + static_cast<int>(e & 0xFFull));
-              buf[i] = (static_cast<unsigned long long>(dd) << 32) | static_cast<uint32_t>(idx);
+          const uint32_t Dstar = bound_from_block_hist(tb.sh_hist, k, lane);
+          if (Dstar < 167u) {
+            const unsigned long long nk = key_bound_of_dist(Dstar);
+            if (nk < thr_key) {
+              thr_key = nk;
+              if (lane == 0) atomicMin(&st->thr_d, Dstar);
             }
-            count_accepted(tb.sh_hist, acc, bal, dd);
-            kept += __popc(bal);
           }
-          __syncwarp();
-          cnt = kept;
-          if (kept == k && buf[k - 1] < thr_key) thr_key = buf[k - 1];
-          flush_hist(tb.sh_hist, st, lane);
-          uint32_t Dstar = bound_from_hist(st, k, lane);
-          if (Dstar < 167u && key_bound_of_dist(Dstar) < thr_key) {
-            thr_key = key_bound_of_dist(Dstar);
-            if (lane == 0) atomicMin(&st->thr_d, Dstar);
-          }
+        };
+        // First tile of the warp: count every record within the bound first and
+        // take the block's bound from those counts, so that only records within
+        // the new bound need their index and a buffer slot.  Counted records left
+        // out lie above a valid bound, hence above the k-th distance, where the
+        // merge needs no exact count.
+        const bool first = j == 0;
+        if (first) {
+#pragma unroll
+          for (int m = 0; m < 4; ++m) count_accepted(tb.sh_hist, c[m], __ballot_sync(kFull, c[m]), d[m]);
+          refresh_bound();
         }
-      } else if (__any_sync(kFull, any)) {
+        const uint32_t Dn = static_cast<uint32_t>(thr_key >> 32);
         bool added = false;
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
           unsigned long long key = ~0ull;
           bool acc = false;
-          if (c[m]) {
+          if (c[m] && d[m] <= Dn) {
             int32_t idx = __ldg(lib.perm + it.tile * kTile + lane + 32 * m);
             key = (static_cast<unsigned long long>(d[m]) << 32) | static_cast<uint32_t>(idx);
             acc = key <= thr_key;
           }
           uint32_t bal = __ballot_sync(kFull, acc);
           if (acc) buf[cnt + __popc(bal & lanemask_lt())] = key;
-          count_accepted(tb.sh_hist, acc, bal, d[m]);
+          if (!first) count_accepted(tb.sh_hist, acc, bal, d[m]);
           cnt += __popc(bal);
           added |= bal != 0;
         }
         __syncwarp();
-        if (added) {
-          flush_hist(tb.sh_hist, st, lane);
-          uint32_t Dstar = bound_from_hist(st, k, lane);
-          if (Dstar < 167u) {
-            unsigned long long nk = key_bound_of_dist(Dstar);
-            if (nk < thr_key) {
-              thr_key = nk;
-              if (lane == 0) atomicMin(&st->thr_d, Dstar);
-            }
-          }
-        }
+        if (added && !first) refresh_bound();
         if (cnt > CAP - kTile) cnt = compact_buffer(buf, cnt, k, thr_key, st, lane);
       }
     }
@@ -609,17 +591,32 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
       mbar_wait_bounded(&bars[j % kStages], static_cast<uint32_t>((j / kStages) & 1), drain_deadline);
   }
 
-  // final per-warp selection, then hand the candidates to the merge
-  cnt = compact_buffer(buf, cnt, k, thr_key, st, lane);
+  // final per-warp selection against the block's latest bound, then hand the
+  // candidates to the merge: one slot reservation per block
   {
-    uint32_t base = 0;
-    if (lane == 0 && cnt > 0) base = atomicAdd(&st->ncand, static_cast<uint32_t>(cnt));
-    base = __shfl_sync(kFull, base, 0);
+    __syncwarp();
+    const uint32_t Db = bound_from_block_hist(tb.sh_hist, k, lane);
+    if (Db < 167u && key_bound_of_dist(Db) < thr_key) thr_key = key_bound_of_dist(Db);
+  }
+  cnt = compact_buffer(buf, cnt, k, thr_key, st, lane);
+  if (lane == 0) tb.wbase[warp] = cnt;
+  __syncthreads();
+  if (tid == 0) {
+    uint32_t tot = 0;
+    for (int w = 0; w < WARPS; ++w) {
+      const int c = tb.wbase[w];
+      tb.wbase[w] = static_cast<int>(tot);
+      tot += static_cast<uint32_t>(c);
+    }
+    tb.blk_base = tot ? atomicAdd(&st->ncand, tot) : 0u;
+  }
+  __syncthreads();
+  {
+    const uint32_t base = tb.blk_base + static_cast<uint32_t>(tb.wbase[warp]);
     for (int i = lane; i < cnt; i += 32) cand[base + i] = buf[i];
   }
 
-  // ---- pending counts to the global histogram, then the last block merges
-  __syncthreads();
+  // ---- the block's counts to the global histogram, then the last block merges
   if (warp == 0) flush_hist(tb.sh_hist, st, lane);
   __threadfence();
   __syncthreads();
@@ -676,15 +673,24 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
   const int cless = tb.cless;
   const int need = k_eff - cless;  // smallest indices still needed at distance T
   const uint32_t ncand = ld_relaxed_u32(&st->ncand);
-  for (uint32_t i = tid; i < ncand; i += blockDim.x) {
-    unsigned long long key = __ldcg(cand + i);
-    uint32_t dd = static_cast<uint32_t>(key >> 32);
-    if (dd < T) {
-      int p = atomicAdd(&tb.nfin, 1);
-      if (p < kFinCap) fin[p] = key;
-    } else if (dd == T) {
-      int p = atomicAdd(&tb.ntie, 1);
-      if (p < kTieCap) ties[p] = key;
+  constexpr int kGather = 8;  // candidate loads in flight per thread
+  for (uint32_t base = 0; base < ncand; base += blockDim.x * kGather) {
+    unsigned long long v[kGather];
+#pragma unroll
+    for (int u = 0; u < kGather; ++u) {
+      const uint32_t i = base + u * blockDim.x + tid;
+      v[u] = i < ncand ? __ldcg(cand + i) : ~0ull;
+    }
+#pragma unroll
+    for (int u = 0; u < kGather; ++u) {
+      const uint32_t dd = static_cast<uint32_t>(v[u] >> 32);
+      if (dd < T) {
+        int p = atomicAdd(&tb.nfin, 1);
+        if (p < kFinCap) fin[p] = v[u];
+      } else if (dd == T) {
+        int p = atomicAdd(&tb.ntie, 1);
+        if (p < kTieCap) ties[p] = v[u];
+      }
     }
   }
   __syncthreads();

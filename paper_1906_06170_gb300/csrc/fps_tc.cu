@@ -10,7 +10,7 @@
 // accumulator is the exact integer q . x and the distances equal the popcount
 // path's.  (sm_103a has no tcgen05 kind::i8, so there is no INT8 variant.)
 //
-// CTA (one per SM, 12 warps):
+// CTA (one per SM, 13 warps):
 //   warp 0  producer: 1-D bulk copies (cp.async.bulk) of the query tile A
 //           (128 x 192 B, double-buffered per work item) and of library tiles B
 //           (256 x 192 B = 48 KB) into a 3-stage ring, completing on mbarriers;
@@ -28,13 +28,15 @@
 //           taken as a 3-input max over the FP16 bit patterns (non-negative
 //           FP16 values order like unsigned integers) per 64 columns.  A lane
 //           whose 64 columns pass hands them, with the bar, to a shared ring;
-//   warp 10 flusher: finishes the compare of ring entries column by column
-//           (8 entries per round, 4 lanes per entry), takes candidate slots with
-//           one returning atomic per entry, appends (distance, position) to the
-//           query's candidate region, counts the query's histogram (the shared
-//           batched state of fps_batch.cu), and every 4 accepted records of a
-//           query asks for its bound to be re-derived;
-//   warp 11 refresher: re-derives a query's bound (smallest D with at least k
+//   warps 10, 11 flushers, taking alternate 32-slot blocks of the ring: each
+//           finishes the compare of up to 32 ring entries per round (one lane
+//           per entry, 64 columns), takes each entry's candidate slots with one
+//           returning atomic (all in flight together), then the warp appends
+//           the round's accepted (distance, position) records to their queries'
+//           candidate regions, 32 at a time, and counts them in the queries'
+//           histograms (the shared batched state of fps_batch.cu); every 4
+//           accepted records of a query it asks for the bound to be re-derived;
+//   warp 12 refresher: re-derives a query's bound (smallest D with at least k
 //           accepted records at distance <= D) with a warp-wide prefix sum over
 //           its histogram and publishes it globally (atomicMin) and to the
 //           epilogue through a per-row shared word.
@@ -67,11 +69,13 @@ constexpr int kATileBytes = kTcQ * kKBytes;      // 24576
 constexpr int kBStages = 3;
 constexpr int kChunkTiles = 64;              // library tiles per work item
 constexpr int kEpiWarps = 8;                 // two per TMEM lane quarter, 128 columns each
-constexpr int kFlushWarp = 2 + kEpiWarps;    // drains the candidate queue
-constexpr int kRefWarp = 3 + kEpiWarps;      // re-derives query bounds from the histograms
-constexpr int kThreads = 32 * (4 + kEpiWarps);
-constexpr uint32_t kRefCap = 64;             // pending bound refreshes per CTA
-constexpr uint32_t kRingCap = 128;           // epilogue hand-offs in flight per CTA
+constexpr int kFlushWarps = 2;               // drain the hand-off ring, alternate 32-slot blocks
+constexpr int kFlushWarp0 = 2 + kEpiWarps;   // first flusher
+constexpr int kRefWarp = kFlushWarp0 + kFlushWarps;   // re-derives query bounds from the histograms
+constexpr int kThreads = 32 * (kRefWarp + 1);
+constexpr uint32_t kRefCap = 32;             // pending bound refreshes per flusher
+constexpr uint32_t kRingCap = 192;           // epilogue hand-offs in flight per CTA
+static_assert(kRingCap % (32 * kFlushWarps) == 0, "ring blocks alternate between the flushers");
 constexpr uint32_t kTmemCols = 512;
 
 // ------------------------------------------------------------------ PTX helpers
@@ -118,6 +122,17 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Hand-off words in shared memory: a release store publishes the writer's earlier
+// stores, an acquire load orders the reader's later loads after it (no full fence).
+__device__ __forceinline__ uint32_t ld_acquire_smem(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.cta.shared::cta.u32 %0, [%1];" : "=r"(v) : "r"(smem_addr(p)) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_smem(uint32_t* p, uint32_t v) {
+  asm volatile("st.release.cta.shared::cta.u32 [%0], %1;" ::"r"(smem_addr(p)), "r"(v) : "memory");
+}
 
 // Shared-memory matrix descriptor: K-major, no swizzle (layout type 0).
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
@@ -238,12 +253,14 @@ __global__ void tc_pack_queries_kernel(const uint64_t* q, int Q, uint8_t* op, in
 // One epilogue lane's 64 FP16 accumulators (a query against 64 records) that
 // passed the tile-level test, with what the flusher needs to finish the compare:
 //   m0 = need (FP16 bit pattern) | valid columns << 16,
-//   m1 = popc q + popc x | item sequence << 9,  pos0 = layout position of column 0;
+//   m1 = popc q + popc x | item sequence << 9,  pos0 = layout position of column 0,
+//   coff, cap = the query's candidate region (first key, keys);
 // seq = ring slot + 1 once written.
 struct RingEntry {
   uint4 v[8];
   uint32_t q, m0, m1, pos0;
-  uint32_t seq, pad[3];
+  uint32_t seq, cap;
+  unsigned long long coff;
 };
 static_assert(sizeof(RingEntry) == 160, "ring entry layout");
 
@@ -262,32 +279,61 @@ struct TcSmem {
   // item and, within it, the smallest bound
   unsigned long long thr_w[kTcQ];
   uint32_t pend[kTcQ];             // accepted records per row (refresh every 4)
-  uint2 ref_q[kRefCap];            // refresh requests (query, item sequence)
+  uint2 ref_q[kFlushWarps][kRefCap];   // refresh requests (query, item sequence), one queue per flusher
   uint32_t r_tail;                 // ring slots claimed by the epilogue
-  uint32_t r_head;                 // ring slots retired by the flusher
+  uint32_t f_head[kFlushWarps];    // next slot each flusher retires; slots below the minimum are free
   uint32_t epi_done;               // epilogue warps finished
-  uint32_t ref_tail;               // refresh requests posted (flusher)
-  uint32_t ref_head;               // refresh requests done (refresher)
-  uint32_t flush_done;             // flusher finished
+  uint32_t ref_tail[kFlushWarps];  // refresh requests posted (per flusher)
+  uint32_t ref_head[kFlushWarps];  // refresh requests done (refresher)
+  uint32_t flush_done;             // flushers finished
 };
 static_assert(sizeof(TcSmem) + 1024 <= 232448, "shared memory per CTA");
 
+// Every ring slot below this one is retired.  A flusher never passes a slot that
+// is claimed and unwritten, so the minimum of the heads is at most any such slot.
+__device__ __forceinline__ uint32_t ring_retired(const TcSmem& S) {
+  uint32_t m = ld_acquire_smem(&S.f_head[0]);
+#pragma unroll
+  for (int f = 1; f < kFlushWarps; ++f) m = min(m, ld_acquire_smem(&S.f_head[f]));
+  return m;
+}
+
 // Epilogue side: claim a ring slot, wait (bounded) for room, write the entry.
 __device__ __forceinline__ bool ring_push(TcSmem& S, const uint32_t (&w)[32], uint32_t q, uint32_t m0, uint32_t m1,
-                                          uint32_t pos0, uint64_t timeout_ns) {
+                                          uint32_t pos0, unsigned long long coff, uint32_t cap,
+                                          uint64_t timeout_ns) {
   const uint32_t slot = atomicAdd(&S.r_tail, 1u);
-  if (slot - *reinterpret_cast<volatile uint32_t*>(&S.r_head) >= kRingCap) {
+  if (slot - ring_retired(S) >= kRingCap) {
+    // the ring is full: wait without taking issue slots from the flushers
     const uint64_t deadline = global_ns() + timeout_ns;
-    while (slot - *reinterpret_cast<volatile uint32_t*>(&S.r_head) >= kRingCap)
+    while (slot - ring_retired(S) >= kRingCap) {
       if (global_ns() > deadline) return false;
+      __nanosleep(64);
+    }
   }
   RingEntry& e = S.ring[slot % kRingCap];
 #pragma unroll
   for (int i = 0; i < 8; ++i) e.v[i] = make_uint4(w[4 * i], w[4 * i + 1], w[4 * i + 2], w[4 * i + 3]);
   *reinterpret_cast<uint4*>(&e.q) = make_uint4(q, m0, m1, pos0);
-  __threadfence_block();
-  *reinterpret_cast<volatile uint32_t*>(&e.seq) = slot + 1;
+  e.cap = cap;
+  e.coff = coff;
+  st_release_smem(&e.seq, slot + 1);
   return true;
+}
+
+// Position of the (r+1)-th set bit of m (r < popc(m)).
+__device__ __forceinline__ int nth_set_bit(uint32_t m, uint32_t r) {
+  int pos = 0;
+#pragma unroll
+  for (int sh = 16; sh > 0; sh >>= 1) {
+    const uint32_t low = static_cast<uint32_t>(__popc(m & ((1u << sh) - 1u)));
+    if (r >= low) {
+      r -= low;
+      m >>= sh;
+      pos += sh;
+    }
+  }
+  return pos;
 }
 
 // Bucket of tensor tile T (tiles of one bucket are contiguous).
@@ -329,10 +375,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     mbar_init(&S.fin, 1);
     S.r_tail = 0;
-    S.r_head = 0;
+    for (int f = 0; f < kFlushWarps; ++f) {
+      S.f_head[f] = 32u * f;
+      S.ref_tail[f] = 0;
+      S.ref_head[f] = 0;
+    }
     S.epi_done = 0;
-    S.ref_tail = 0;
-    S.ref_head = 0;
     S.flush_done = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -444,7 +492,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       mma_commit(&S.fin);
       mbar_wait(&S.fin, 0, timeout_ns);
     }
-  } else if (warp < kFlushWarp) {
+  } else if (warp < kFlushWarp0) {
     // -------------------------------------------------------------- epilogue
     const int ew = warp - 2;
     const int quarter = warp & 3;                 // TMEM lanes 32*quarter .. +31
@@ -461,10 +509,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int q = qt * kTcQ + row;
       const bool live = q < b.Q && b.k[q] > 0;
       int pq = 0;
-      uint32_t thr = 0;
+      uint32_t thr = 0, ccap = 0;
+      unsigned long long coff = 0;
       const unsigned long long jkey = static_cast<unsigned long long>(j) << 32;
       if (live) {
         pq = __popcll(b.queries[3 * q]) + __popcll(b.queries[3 * q + 1]) + __popcll(b.queries[3 * q + 2]);
+        coff = static_cast<unsigned long long>(b.cand_off[q]);
+        ccap = static_cast<uint32_t>(b.cand_off[q + 1] - b.cand_off[q]);
         thr = ld_relaxed_u32(b.thr + q);
         atomicMax(&S.thr_w[row], jkey | (0xFFFFFFFFu - thr));
       }
@@ -521,7 +572,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (lim <= 0) return;
             if (!ring_push(S, w, static_cast<uint32_t>(q), need16 | (static_cast<uint32_t>(lim) << 16),
                            static_cast<uint32_t>(pq + bk) | (static_cast<uint32_t>(j) << 9),
-                           static_cast<uint32_t>(T * kTcRows + colb), deadline))
+                           static_cast<uint32_t>(T * kTcRows + colb), coff, ccap, deadline))
               ok = false;
           };
           group(v[0], 0);
@@ -533,22 +584,44 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (!ok && lane == 0) atomicOr(b.err, DEVERR_TIMEOUT);
     __syncwarp();
     if (lane == 0) atomicAdd(&S.epi_done, 1u);
-  } else if (warp == kFlushWarp) {
-    // ---------------------------------------------------------------- flusher
-    // Up to 8 ring entries per round, 4 lanes per entry (8 registers = 16 columns
-    // each): exact compare, one returning atomic per entry for candidate slots,
-    // histogram counts, and a bound refresh request every 4 accepted records.
-    uint32_t head = 0, rtail = 0;
+  } else if (warp < kRefWarp) {
+    // --------------------------------------------------------------- flushers
+    // Flusher f takes the ring's 32-slot blocks f, f + kFlushWarps, ...  Up to 32
+    // ring entries per round, one lane per entry: the exact compare of the
+    // entry's 64 columns and one returning atomic for its candidate slots, all
+    // entries' atomics in flight together; then the round's accepted records are
+    // written by the whole warp, 32 at a time (candidate, histogram count), and
+    // a bound refresh is requested every 4 accepted records of a query.
+    const int fw = warp - kFlushWarp0;
+    uint32_t head = 32u * static_cast<uint32_t>(fw), rtail = 0;
     uint64_t idle_since = 0;
-    const int g = lane >> 2, sub = lane & 3;
+    // The ring entries of a round are released before the round's slot
+    // reservations return: each lane keeps at most one accepted record of the
+    // previous round (p_*), written once the owner entry's reservation (e_*)
+    // is in, at the start of the next round or when the warp goes idle.
+    bool pv = false;
+    int p_own = 0;
+    uint32_t p_r = 0, p_d = 0, p_pos = 0;
+    uint32_t e_base = 0, e_cap = 0;
+    long long e_coff = 0;
+    auto write_pending = [&]() {
+      const uint32_t obase = __shfl_sync(kFull, e_base, p_own);
+      const uint32_t ocap = __shfl_sync(kFull, e_cap, p_own);
+      const long long ocoff = __shfl_sync(kFull, e_coff, p_own);
+      if (pv && obase + p_r < ocap) b.cand[ocoff + obase + p_r] = (static_cast<unsigned long long>(p_d) << 32) | p_pos;
+      pv = false;
+    };
     for (;;) {
-      const uint32_t idx = head + static_cast<uint32_t>(lane & 7);
-      const bool ready = *reinterpret_cast<volatile uint32_t*>(&S.ring[idx % kRingCap].seq) == idx + 1;
-      const uint32_t bal = __ballot_sync(kFull, ready) & 0xFFu;
-      const int n = bal == 0xFFu ? 8 : __ffs(~bal) - 1;   // ready entries in a row from head
+      const uint32_t idx = head + static_cast<uint32_t>(lane);
+      const bool ready = idx < ((head & ~31u) + 32u) &&   // within this flusher's current block
+                         ld_acquire_smem(&S.ring[idx % kRingCap].seq) == idx + 1;
+      const uint32_t bal = __ballot_sync(kFull, ready);
+      const int n = bal == kFull ? 32 : __ffs(~bal) - 1;   // ready entries in a row from head
       if (n == 0) {
+        write_pending();
         const bool epi_over = *reinterpret_cast<volatile uint32_t*>(&S.epi_done) == kEpiWarps;
-        if (epi_over && *reinterpret_cast<volatile uint32_t*>(&S.r_tail) == head) break;
+        // every claimed slot of this flusher's blocks is below head
+        if (epi_over && *reinterpret_cast<volatile uint32_t*>(&S.r_tail) <= head) break;
         // idle: wait for the epilogue (itself bounded); claimed-but-unwritten slots after
         // it finished get timeout_ns, and no idle spell may exceed 32 x timeout_ns
         const uint64_t now = global_ns();
@@ -561,103 +634,147 @@ __global__ void __launch_bounds__(kThreads, 1)
         continue;
       }
       idle_since = 0;
-      __threadfence_block();
-      const bool mine = g < n;
-      const RingEntry& e = S.ring[(head + static_cast<uint32_t>(g)) % kRingCap];
-      uint32_t eq = 0, m0 = 0, m1 = 0, pos0 = 0;
-      uint32_t w[8];
+      const bool mine = lane < n;
+      const RingEntry& e = S.ring[idx % kRingCap];
+      uint32_t eq = 0, m0 = 0, m1 = 0, pos0 = 0, ecap = 0;
+      unsigned long long ecoff = 0;
+      uint32_t hlo = 0, hhi = 0;   // bit c of (hhi:hlo): column c passes
       if (mine) {
         const uint4 mt = *reinterpret_cast<const uint4*>(&e.q);
         eq = mt.x;
         m0 = mt.y;
         m1 = mt.z;
         pos0 = mt.w;
-        const uint4 a0 = e.v[2 * sub], a1 = e.v[2 * sub + 1];
-        w[0] = a0.x; w[1] = a0.y; w[2] = a0.z; w[3] = a0.w;
-        w[4] = a1.x; w[5] = a1.y; w[6] = a1.z; w[7] = a1.w;
-      }
-      const uint32_t need16 = m0 & 0xFFFFu, need2 = need16 | (need16 << 16);
-      const int lim = static_cast<int>(m0 >> 16);
-      // halves are below 0x8000: (w | 0x80008000) - need2 borrows across neither half and
-      // leaves bit 15 (31) set exactly where the low (high) half is >= need
-      uint32_t hits = 0;   // bit i: column 16 sub + i passes
+        ecap = e.cap;
+        ecoff = e.coff;
+        const uint32_t need16 = m0 & 0xFFFFu, need2 = need16 | (need16 << 16);
+        // halves are below 0x8000: (w | 0x80008000) - need2 borrows across neither half and
+        // leaves bit 15 (31) set exactly where the low (high) half is >= need
 #pragma unroll
-      for (int r = 0; r < 8; ++r) {
-        const uint32_t t = ((w[r] | 0x80008000u) - need2) & 0x80008000u;
-        hits |= ((t >> 15) & 1u) << (2 * r);
-        hits |= (t >> 31) << (2 * r + 1);
+        for (int i = 0; i < 8; ++i) {
+          const uint4 a4 = e.v[i];
+          const uint32_t ww[4] = {a4.x, a4.y, a4.z, a4.w};
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int r = 4 * i + u;   // word r holds columns 2r (low half) and 2r + 1 (high half)
+            const uint32_t t = ((ww[u] | 0x80008000u) - need2) & 0x80008000u;
+            const uint32_t two = ((t >> 15) & 1u) | ((t >> 30) & 2u);
+            if (r < 16)
+              hlo |= two << (2 * r);
+            else
+              hhi |= two << (2 * (r - 16));
+          }
+        }
+        const int lim = static_cast<int>(m0 >> 16);   // valid columns, 1..64
+        if (lim <= 32) {
+          hhi = 0;
+          if (lim < 32) hlo &= (1u << lim) - 1u;
+        } else if (lim < 64) {
+          hhi &= (1u << (lim - 32)) - 1u;
+        }
       }
-      const int c0 = 16 * sub;
-      if (!mine || lim <= c0) hits = 0;
-      else if (lim < c0 + 16) hits &= (1u << (lim - c0)) - 1u;
-      const uint32_t cnt = __popc(hits);
-      // exclusive prefix of the counts over the 4 lanes of this entry
-      uint32_t incl = cnt;
-      {
-        const uint32_t y1 = __shfl_up_sync(kFull, incl, 1);
-        if (sub >= 1) incl += y1;
-        const uint32_t y2 = __shfl_up_sync(kFull, incl, 2);
-        if (sub >= 2) incl += y2;
-      }
-      const uint32_t total = __shfl_sync(kFull, incl, (lane & ~3) + 3);
-      uint32_t base = 0;
+      const uint32_t cnt = static_cast<uint32_t>(__popc(hlo) + __popc(hhi));
+      write_pending();   // the previous round's reservations are needed before they are replaced
       bool req = false;
-      if (mine && sub == 0 && total > 0) {
-        base = atomicAdd(b.cnt + eq, total);
-        const uint32_t old = atomicAdd(&S.pend[eq % kTcQ], total);
-        req = (old >> 2) != ((old + total) >> 2);
+      if (cnt > 0) {
+        e_base = atomicAdd(b.cnt + eq, cnt);
+        const uint32_t old = atomicAdd(&S.pend[eq % kTcQ], cnt);
+        req = (old >> 2) != ((old + cnt) >> 2);
+        e_coff = static_cast<long long>(ecoff);
+        e_cap = ecap;
       }
-      base = __shfl_sync(kFull, base, lane & ~3);
-      if (hits) {
-        const int64_t off = b.cand_off[eq], cap = b.cand_off[eq + 1] - off;
-        uint32_t slot = base + incl - cnt;
-        uint32_t* hq = b.hist + static_cast<size_t>(eq) * 168;
-        const int dbase = static_cast<int>(m1 & 0x1FFu);
-        while (hits) {
-          const int i = __ffs(hits) - 1;
-          hits &= hits - 1;
-          uint32_t x = 0;
+      // this entry's first record among the round's accepted records
+      uint32_t incl = cnt;
 #pragma unroll
-          for (int r = 0; r < 8; ++r) x |= w[r] & (0u - static_cast<uint32_t>(r == (i >> 1)));
-          const uint32_t h16 = (i & 1) ? (x >> 16) : (x & 0xFFFFu);
-          const int a = static_cast<int>(__half2float(__ushort_as_half(static_cast<unsigned short>(h16))));
-          const uint32_t d = static_cast<uint32_t>(dbase - 2 * a);
-          red_add_u32(hq + d, 1u);
-          if (slot < cap) b.cand[off + slot] = (static_cast<unsigned long long>(d) << 32) | (pos0 + c0 + i);
-          ++slot;
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const uint32_t off = incl - cnt;
+      const uint32_t total = __shfl_sync(kFull, incl, 31);
+      const bool defer = total <= 32;   // one record per lane: written next round
+      __syncwarp();   // every lane may read every entry of the round (each owner acquired its own)
+      for (uint32_t h0 = 0; h0 < total; h0 += 32) {
+        const uint32_t h = h0 + static_cast<uint32_t>(lane);
+        // owner: the last entry whose first record is <= h (it has records when h < total)
+        int own = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+          const uint32_t o2 = __shfl_sync(kFull, off, own + step);
+          if (o2 <= h) own += step;
+        }
+        const uint32_t r = h - __shfl_sync(kFull, off, own);
+        const uint32_t olo = __shfl_sync(kFull, hlo, own), ohi = __shfl_sync(kFull, hhi, own);
+        const uint32_t oq = __shfl_sync(kFull, eq, own), om1 = __shfl_sync(kFull, m1, own);
+        const uint32_t opos = __shfl_sync(kFull, pos0, own);
+        uint32_t d = 0, pos = 0;
+        if (h < total) {
+          const uint32_t nlo = static_cast<uint32_t>(__popc(olo));
+          const int col = r < nlo ? nth_set_bit(olo, r) : 32 + nth_set_bit(ohi, r - nlo);
+          const uint16_t* vals = reinterpret_cast<const uint16_t*>(S.ring[(head + own) % kRingCap].v);
+          const int a = static_cast<int>(__half2float(__ushort_as_half(vals[col])));
+          d = static_cast<uint32_t>(static_cast<int>(om1 & 0x1FFu) - 2 * a);
+          pos = opos + static_cast<uint32_t>(col);
+          red_add_u32(b.hist + static_cast<size_t>(oq) * 168 + d, 1u);
+        }
+        if (defer) {
+          pv = h < total;
+          p_own = own;
+          p_r = r;
+          p_d = d;
+          p_pos = pos;
+        } else {   // more records than lanes: wait for the reservations now
+          const uint32_t obase = __shfl_sync(kFull, e_base, own);
+          const uint32_t ocap = __shfl_sync(kFull, e_cap, own);
+          const long long ocoff = __shfl_sync(kFull, e_coff, own);
+          if (h < total && obase + r < ocap) b.cand[ocoff + obase + r] = (static_cast<unsigned long long>(d) << 32) | pos;
         }
       }
       __syncwarp();
       head += static_cast<uint32_t>(n);
-      if (lane == 0) *reinterpret_cast<volatile uint32_t*>(&S.r_head) = head;
+      if ((head & 31u) == 0) head += 32u * (kFlushWarps - 1);   // over the other flushers' blocks
+      if (lane == 0) st_release_smem(&S.f_head[fw], head);
       // post refresh requests while there is room (a dropped request only delays a bound)
       const uint32_t rb = __ballot_sync(kFull, req);
       if (rb) {
         uint32_t rh = 0;
-        if (lane == 0) rh = *reinterpret_cast<volatile uint32_t*>(&S.ref_head);
+        if (lane == 0) rh = *reinterpret_cast<volatile uint32_t*>(&S.ref_head[fw]);
         const uint32_t room = kRefCap - (rtail - __shfl_sync(kFull, rh, 0));   // one view for the warp
         const uint32_t rank = __popc(rb & ((1u << lane) - 1u));
-        if (req && rank < room) S.ref_q[(rtail + rank) % kRefCap] = make_uint2(eq, m1 >> 9);
+        if (req && rank < room) S.ref_q[fw][(rtail + rank) % kRefCap] = make_uint2(eq, m1 >> 9);
         const uint32_t posted = min(static_cast<uint32_t>(__popc(rb)), room);
-        __threadfence_block();
         __syncwarp();
         rtail += posted;
-        if (lane == 0) *reinterpret_cast<volatile uint32_t*>(&S.ref_tail) = rtail;
+        if (lane == 0) st_release_smem(&S.ref_tail[fw], rtail);
       }
     }
+    write_pending();
     __syncwarp();
-    if (lane == 0) *reinterpret_cast<volatile uint32_t*>(&S.flush_done) = 1u;
+    if (lane == 0) atomicAdd(&S.flush_done, 1u);
   } else if (warp == kRefWarp) {
     // -------------------------------------------------------------- refresher
     // bound = smallest D <= thr with at least k accepted records at distance <= D,
     // from the query's histogram (any subset of its counts gives a valid bound)
-    uint32_t rhead = 0;
+    // (one request from each flusher's queue in turn)
+    uint32_t rhead[kFlushWarps];
+#pragma unroll
+    for (int f = 0; f < kFlushWarps; ++f) rhead[f] = 0;
     uint64_t idle_since = 0;
+    int f = 0;
     for (;;) {
-      const uint32_t rt = *reinterpret_cast<volatile uint32_t*>(&S.ref_tail);
-      if (rt == rhead) {
-        const bool fl_over = *reinterpret_cast<volatile uint32_t*>(&S.flush_done) != 0u;
-        if (fl_over && *reinterpret_cast<volatile uint32_t*>(&S.ref_tail) == rhead) break;
+      int src = -1;
+#pragma unroll
+      for (int i = 0; i < kFlushWarps; ++i) {
+        const int g = (f + i) % kFlushWarps;
+        if (src < 0 && ld_acquire_smem(&S.ref_tail[g]) != rhead[g]) src = g;
+      }
+      if (src < 0) {
+        const bool fl_over = *reinterpret_cast<volatile uint32_t*>(&S.flush_done) == kFlushWarps;
+        bool drained = true;
+#pragma unroll
+        for (int g = 0; g < kFlushWarps; ++g)
+          drained = drained && *reinterpret_cast<volatile uint32_t*>(&S.ref_tail[g]) == rhead[g];
+        if (fl_over && drained) break;
         const uint64_t now = global_ns();
         if (idle_since == 0) idle_since = now;
         if (now - idle_since > 64 * timeout_ns) {
@@ -667,9 +784,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         __nanosleep(512);
         continue;
       }
+      f = (src + 1) % kFlushWarps;
       idle_since = 0;
-      __threadfence_block();
-      const uint2 r = S.ref_q[rhead % kRefCap];
+      uint32_t head_src = 0;
+#pragma unroll
+      for (int g = 0; g < kFlushWarps; ++g) head_src = g == src ? rhead[g] : head_src;
+      const uint2 r = S.ref_q[src][head_src % kRefCap];
       const uint32_t rq = r.x, rj = r.y;
       const uint32_t kq = static_cast<uint32_t>(b.k[rq]);
       const uint32_t tcur = ld_relaxed_u32(b.thr + rq);
@@ -695,8 +815,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         atomicMax(&S.thr_w[rq % kTcQ], (static_cast<unsigned long long>(rj) << 32) | (0xFFFFFFFFu - D));
       }
       __syncwarp();
-      ++rhead;
-      if (lane == 0) *reinterpret_cast<volatile uint32_t*>(&S.ref_head) = rhead;
+#pragma unroll
+      for (int g = 0; g < kFlushWarps; ++g) rhead[g] += g == src ? 1u : 0u;
+      if (lane == 0) *reinterpret_cast<volatile uint32_t*>(&S.ref_head[src]) = head_src + 1;
     }
   }
 

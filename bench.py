@@ -213,6 +213,13 @@ def paper_method_context(records: int = 50_000):
 
 
 # -------------------------------------------------------------- reference
+def workload_config(n: int, ws: int) -> dict:
+    """The default workload's config, shared by both arms."""
+    return {"workload": f"{n:,} generated MACCS-166 fingerprints (seed 0), {QUERIES_PER_STEP} sequential single "
+                        f"queries per step per GPU (seed 1001), k={K}, popcount scan with bucket pruning",
+            "n_records": n, "queries_per_step": QUERIES_PER_STEP, "k": K, "parallelism": f"replicas x{ws}"}
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -235,10 +242,10 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": value / PAPER_GCPS, "dtype": "u8",
             "data": "synthetic",
-            "config": {"workload": f"CPU oracle, one query per step over {records:,} of the {args.n:,} "
-                                   f"generated records, k={K}", "n_records": args.n, "k": K},
+            "config": workload_config(args.n, ws),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                             "sample": f"1 query x {records:,} records per step"},
+                             "sample": f"each step: 1 query (seed 1001) x the first {records:,} of the "
+                                       f"{args.n:,} records, parse + distances on {threads} threads + full sort"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -354,13 +361,9 @@ def run_gb300(args):
                 "vs_baseline_note": "paper: 95,417,114 molecules in ~40 min on an i5-6500 (Sec. 2.2); "
                                     "other hardware, PubChem data -- context only",
                 "dtype": "u64", "data": "synthetic",
-                "config": {"workload": f"{n:,} generated MACCS-166 fingerprints (seed 0), "
-                                       f"{QUERIES_PER_STEP} sequential single queries per step per GPU "
-                                       f"(seed 1001), k={K}, popcount scan with bucket pruning",
-                           "n_records": n, "queries_per_step": QUERIES_PER_STEP, "k": K,
+                "config": {**workload_config(n, ws),
                            "l2": f"library {info['n_tiles'] * 3072 / 1e9:.2f} GB >> 129 MB L2: every "
-                                 "step streams from HBM, no flush needed",
-                           "parallelism": f"replicas x{ws}"},
+                                 "step streams from HBM, no flush needed"},
                 "roofline": roof, "clocks": clk,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": QUERIES_PER_STEP * 24,
                         "d2h_bytes_per_step": QUERIES_PER_STEP * (4 + 8 * K) + 4},

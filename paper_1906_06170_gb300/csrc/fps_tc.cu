@@ -521,6 +521,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       const int64_t t0 = c * kChunkTiles, t1 = min(t0 + kChunkTiles, n_tc);
       bk = bucket_of(S.tile_off2, t0);
+      // other CTAs' refreshes of this query reach the row through the global
+      // bound, re-read every 8 tiles (loaded one tile before it is used)
+      uint32_t gthr = thr;
       for (int64_t T = t0; T < t1; ++T, ++tn) {
         const int acc = static_cast<int>(tn & 1);
         if (live) {   // the refresher may have tightened this row's bound
@@ -529,6 +532,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t t = 0xFFFFFFFFu - static_cast<uint32_t>(w);
             thr = t < thr ? t : thr;
           }
+          if (((T - t0) & 7) == 1) thr = gthr < thr ? gthr : thr;
+          if (((T - t0) & 7) == 0) gthr = ld_relaxed_u32(b.thr + q);
         }
         while (bk + 1 < kNumBuckets && S.tile_off2[bk + 1] <= T) ++bk;
         int nvalid = S.bcount[bk] - static_cast<int>(T - S.tile_off2[bk]) * kTcRows;

@@ -62,13 +62,17 @@ struct WideLib {
   int W;
 };
 
+// The bound (read by every warp after every tile) and the tile counter (one
+// atomic per claim) sit on separate 128-byte lines.
 struct WideState {
   unsigned long long thr_key;   // global bound on the k-th key
   unsigned int ncand;           // unused (kept zero)
   unsigned int done;            // blocks finished
+  unsigned int pad0[28];
   unsigned int next_tile;       // tile counter
-  unsigned int pad[3];
+  unsigned int pad1[31];
 };
+static_assert(sizeof(WideState) == 256, "scan state fills its 256-byte slot");
 
 __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
   unsigned long long v;

@@ -534,13 +534,13 @@ def run_batch(args):
     if args.path in ("tc_fp8", "popc_batch"):
         plan = fps.fps_batch_plan_create(lib, ks, path=paths[args.path])
         for _ in range(2):
-            fps.fps_batch_plan_run(plan, qs)
+            fps.fps_batch_plan_run(plan, qs, flat=True)
         t_e = time.perf_counter()
         e2e_steps = max(2, min(args.steps, 5))
         for _ in range(e2e_steps):
-            res = fps.fps_batch_plan_run(plan, qs)
+            ri, rd, rc, ro = fps.fps_batch_plan_run(plan, qs, flat=True)
         e2e_s = (time.perf_counter() - t_e) / e2e_steps
-        assert all(len(r[0]) == min(int(kk), n) for r, kk in zip(res, ks)), "plan results malformed"
+        assert np.array_equal(rc, np.minimum(ks, n)), "plan results malformed"
         fps.fps_batch_plan_release(plan)
         e2e = {"value": Q * n / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": Q * 24,
                "d2h_bytes_per_step": int(np.sum(ks)) * 8 + Q * 4, "ms_per_step": e2e_s * 1e3,

@@ -268,10 +268,12 @@ def batch_offsets(k) -> np.ndarray:
 
 
 def fps_search_batch(lib: Library, queries, k, *, path: int = FPS_PATH_AUTO, out_index=None, out_dist=None,
-                     out_count=None, offsets=None, tau=None, timeout_s: float = 0.0, stream=None, stats=None):
+                     out_count=None, offsets=None, tau=None, timeout_s: float = 0.0, stream=None, stats=None,
+                     flat: bool = False):
     """Many packed queries (Q x 3 uint64) with per-query k (host array or scalar).
 
-    Host form (NumPy queries): returns a list of (index, distance) per query.
+    Host form (NumPy queries): returns a list of (index, distance) per query, or with flat=True
+    the arrays (index, distance, count, offsets) without per-query copies.
     Device form (CUDA tensor queries): outputs are CUDA int32 tensors laid out
     by ``offsets`` (prefix sums of k); asynchronous; returns
     (out_index, out_dist, out_count, offsets).
@@ -309,6 +311,8 @@ def fps_search_batch(lib: Library, queries, k, *, path: int = FPS_PATH_AUTO, out
     st = _lib.fps_search_batch(lib._h, q.ctypes.data, Q, kk.ctypes.data, off.ctypes.data, idx.ctypes.data,
                                dist.ctypes.data, cnt.ctypes.data, ctypes.byref(o), _stream_ptr(stream))
     _check(st, "fps_search_batch")
+    if flat:
+        return idx, dist, cnt, off
     return [(idx[off[i]: off[i] + cnt[i]].copy(), dist[off[i]: off[i] + cnt[i]].copy()) for i in range(Q)]
 
 
@@ -511,8 +515,10 @@ def fps_batch_plan_create(lib: Library, k, path: int = FPS_PATH_AUTO, learned: b
     return BatchPlan(h.value, kk)
 
 
-def fps_batch_plan_run(plan: BatchPlan, queries, tau=None, stats=None, stream=None):
-    """Run a captured batch on host queries [Q, 3]; returns a list of (index, distance) per query."""
+def fps_batch_plan_run(plan: BatchPlan, queries, tau=None, stats=None, stream=None, flat: bool = False):
+    """Run a captured batch on host queries [Q, 3]; returns a list of (index, distance) per query, or with
+    flat=True the arrays (index, distance, count, offsets): query i's results are
+    index[offsets[i]: offsets[i] + count[i]] (no per-query copies)."""
     q = np.ascontiguousarray(np.asarray(queries, dtype=np.uint64).reshape(-1, FPS_WORDS))
     Q = plan.k.size
     total = max(int(plan.off[-1]), 1)
@@ -523,6 +529,8 @@ def fps_batch_plan_run(plan: BatchPlan, queries, tau=None, stats=None, stream=No
                                    idx.ctypes.data, dist.ctypes.data, cnt.ctypes.data, ctypes.byref(st_obj),
                                    _stream_ptr(stream)), "fps_batch_plan_run")
     off = plan.off
+    if flat:
+        return idx, dist, cnt, off
     return [(idx[off[i]: off[i] + cnt[i]].copy(), dist[off[i]: off[i] + cnt[i]].copy()) for i in range(Q)]
 
 

@@ -46,6 +46,12 @@ def test_batch_popc_small_libraries(gpu_lib, n):
         check_batch(fps, lib, text, qs, ks, fps.FPS_PATH_POPC_BATCH)
         check_batch(fps, lib, text, qs, ks, fps.FPS_PATH_POPC_BATCH, device_io=True)
         check_batch(fps, lib, text, qs, ks, fps.FPS_PATH_AUTO)
+        # the flat host form returns the same records without per-query copies (k may exceed n)
+        lists = fps.fps_search_batch(lib, qs, ks, path=fps.FPS_PATH_POPC_BATCH)
+        fi, fd, fc, fo = fps.fps_search_batch(lib, qs, ks, path=fps.FPS_PATH_POPC_BATCH, flat=True)
+        for q, (gi, gd) in enumerate(lists):
+            assert fc[q] == len(gi) == min(int(ks[q]), n)
+            assert np.array_equal(fi[fo[q]: fo[q] + fc[q]], gi) and np.array_equal(fd[fo[q]: fo[q] + fc[q]], gd)
     finally:
         fps.fps_release(lib)
 

@@ -28,6 +28,12 @@ def test_plan_runs_repeatedly_with_new_queries(gpu_lib, path_name):
                 want = oracle.topk_many(text, qstrs(qs), ks)
                 for (gi, gd), (wi, wd) in zip(got, want):
                     assert np.array_equal(gi, wi) and np.array_equal(gd, wd)
+                # the flat form: one index / distance array laid out by the k prefix sums
+                fi, fd, fc, fo = fps.fps_batch_plan_run(plan, qs, flat=True)
+                assert np.array_equal(fo, fps.batch_offsets(ks))
+                for q, (wi, wd) in enumerate(want):
+                    assert fc[q] == len(wi)
+                    assert np.array_equal(fi[fo[q]: fo[q] + fc[q]], wi) and np.array_equal(fd[fo[q]: fo[q] + fc[q]], wd)
         finally:
             fps.fps_batch_plan_release(plan)
     finally:

@@ -760,26 +760,22 @@ __global__ void __launch_bounds__(kThreads, 1)
     // -------------------------------------------------------------- refresher
     // bound = smallest D <= thr with at least k accepted records at distance <= D,
     // from the query's histogram (any subset of its counts gives a valid bound)
-    // (one request from each flusher's queue in turn)
-    uint32_t rhead[kFlushWarps];
-#pragma unroll
-    for (int f = 0; f < kFlushWarps; ++f) rhead[f] = 0;
+    // (one request from each flusher's queue in turn; two scalar queue heads, which an
+    // array indexed by the queue number would have put in local memory)
+    static_assert(kFlushWarps == 2, "the refresher polls two request queues");
+    uint32_t rh0 = 0, rh1 = 0;
     uint64_t idle_since = 0;
     int f = 0;
     for (;;) {
-      int src = -1;
-#pragma unroll
-      for (int i = 0; i < kFlushWarps; ++i) {
-        const int g = (f + i) % kFlushWarps;
-        if (src < 0 && ld_acquire_smem(&S.ref_tail[g]) != rhead[g]) src = g;
-      }
+      const uint32_t t0v = ld_acquire_smem(&S.ref_tail[0]), t1v = ld_acquire_smem(&S.ref_tail[1]);
+      int src;
+      if (f == 0)
+        src = t0v != rh0 ? 0 : (t1v != rh1 ? 1 : -1);
+      else
+        src = t1v != rh1 ? 1 : (t0v != rh0 ? 0 : -1);
       if (src < 0) {
         const bool fl_over = *reinterpret_cast<volatile uint32_t*>(&S.flush_done) == kFlushWarps;
-        bool drained = true;
-#pragma unroll
-        for (int g = 0; g < kFlushWarps; ++g)
-          drained = drained && *reinterpret_cast<volatile uint32_t*>(&S.ref_tail[g]) == rhead[g];
-        if (fl_over && drained) break;
+        if (fl_over && t0v == rh0 && t1v == rh1) break;
         const uint64_t now = global_ns();
         if (idle_since == 0) idle_since = now;
         if (now - idle_since > 64 * timeout_ns) {
@@ -789,11 +785,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         __nanosleep(512);
         continue;
       }
-      f = (src + 1) % kFlushWarps;
+      f = src ^ 1;
       idle_since = 0;
-      uint32_t head_src = 0;
-#pragma unroll
-      for (int g = 0; g < kFlushWarps; ++g) head_src = g == src ? rhead[g] : head_src;
+      const uint32_t head_src = src == 0 ? rh0 : rh1;
       const uint2 r = S.ref_q[src][head_src % kRefCap];
       const uint32_t rq = r.x, rj = r.y;
       const uint32_t kq = static_cast<uint32_t>(b.k[rq]);
@@ -820,8 +814,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         atomicMax(&S.thr_w[rq % kTcQ], (static_cast<unsigned long long>(rj) << 32) | (0xFFFFFFFFu - D));
       }
       __syncwarp();
-#pragma unroll
-      for (int g = 0; g < kFlushWarps; ++g) rhead[g] += g == src ? 1u : 0u;
+      if (src == 0)
+        ++rh0;
+      else
+        ++rh1;
       if (lane == 0) *reinterpret_cast<volatile uint32_t*>(&S.ref_head[src]) = head_src + 1;
     }
   }

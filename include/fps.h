@@ -24,8 +24,10 @@
  *     fps_release must not race searches still in flight (the caller's duty);
  *   - bit order of a packed record or query: key j (character j of the text
  *     line, 0-based) is bit j % 64 of 64-bit word j / 64; bits 166..191 are 0;
- *   - k = 0 is valid and returns no results; out_count = min(k, N); result
- *     slots past out_count are left untouched;
+ *   - k = 0 is valid and returns no results; out_count = min(k, N); the
+ *     result slots from out_count up to k (k > N) hold -1 in every output
+ *     array (index, distance, CID); slots past k, where the offsets of a
+ *     batched call leave room, are left untouched;
  *   - k may not exceed FPS_K_MAX (FPS_ERR_UNSUPPORTED otherwise).
  */
 #ifndef FPS_H

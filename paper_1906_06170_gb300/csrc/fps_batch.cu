@@ -278,6 +278,10 @@ __global__ void __launch_bounds__(kSelThreads) batch_select_kernel(DevLib lib, B
   const int k = b.k[q];
   const int64_t ob = b.out_off[q];
   if (k <= 0 || lib.n == 0) {
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {   // an empty library: every slot holds -1
+      b.out_idx[ob + i] = -1;
+      b.out_dist[ob + i] = -1;
+    }
     if (threadIdx.x == 0) b.out_count[q] = 0;
     return;
   }
@@ -380,9 +384,9 @@ __global__ void __launch_bounds__(kSelThreads) batch_select_kernel(DevLib lib, B
   for (int i = k_eff + threadIdx.x; i < p; i += blockDim.x) fin[i] = ~0ull;
   __syncthreads();
   block_bitonic_sort(fin, p);
-  for (int i = threadIdx.x; i < k_eff; i += blockDim.x) {
-    b.out_idx[ob + i] = static_cast<int32_t>(fin[i] & 0xFFFFFFFFull);
-    b.out_dist[ob + i] = static_cast<int32_t>(fin[i] >> 32);
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {   // slots past k_eff hold -1
+    b.out_idx[ob + i] = i < k_eff ? static_cast<int32_t>(fin[i] & 0xFFFFFFFFull) : -1;
+    b.out_dist[ob + i] = i < k_eff ? static_cast<int32_t>(fin[i] >> 32) : -1;
   }
   if (threadIdx.x == 0) b.out_count[q] = k_eff;
 }
@@ -445,13 +449,14 @@ namespace {
 // round the smallest key (distance << 32 | global index) over the lanes is
 // written and its lane advances.  Indices of different shards never collide,
 // so the keys are distinct and the order is the total (distance, index) order.
-__global__ void shard_merge_kernel(ShardLists sl, int Q, const int64_t* __restrict__ off, int32_t* __restrict__ out_idx,
+__global__ void shard_merge_kernel(ShardLists sl, int Q, const int64_t* __restrict__ off,
+                                   const int32_t* __restrict__ k, int32_t* __restrict__ out_idx,
                                    int32_t* __restrict__ out_dist, int32_t* __restrict__ out_count) {
   const int lane = threadIdx.x & 31;
   const int q = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (q >= Q) return;
   const int64_t o = off[q];
-  const int kq = static_cast<int>(off[q + 1] - o);
+  const int kq = k[q];   // the slots from off[q] on may be more than k[q]; the results are not
   int cnt = 0, p = 0;
   if (lane < sl.n) cnt = sl.count[lane][q];
   auto key_at = [&](int i) -> unsigned long long {
@@ -477,6 +482,10 @@ __global__ void shard_merge_kernel(ShardLists sl, int Q, const int64_t* __restri
       head = p < cnt ? key_at(p) : ~0ull;
     }
   }
+  for (int i = n_out + lane; i < kq; i += 32) {   // slots past the merged count, up to k, hold -1
+    out_idx[o + i] = -1;
+    out_dist[o + i] = -1;
+  }
   if (lane == 0) out_count[q] = n_out;
 }
 
@@ -486,11 +495,11 @@ __global__ void progress_kernel(int64_t* slot, int64_t value) {
 
 }  // namespace
 
-cudaError_t launch_shard_merge(const ShardLists& sl, int Q, const int64_t* off, int32_t* out_idx, int32_t* out_dist,
-                               int32_t* out_count, cudaStream_t s) {
+cudaError_t launch_shard_merge(const ShardLists& sl, int Q, const int64_t* off, const int32_t* k, int32_t* out_idx,
+                               int32_t* out_dist, int32_t* out_count, cudaStream_t s) {
   if (Q <= 0) return cudaSuccess;
   const int warps = 8;
-  shard_merge_kernel<<<(Q + warps - 1) / warps, 32 * warps, 0, s>>>(sl, Q, off, out_idx, out_dist, out_count);
+  shard_merge_kernel<<<(Q + warps - 1) / warps, 32 * warps, 0, s>>>(sl, Q, off, k, out_idx, out_dist, out_count);
   return cudaGetLastError();
 }
 

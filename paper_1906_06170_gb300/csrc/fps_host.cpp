@@ -436,10 +436,19 @@ fps_status take_device_error(Workspace* w, cudaStream_t s) {
 
 double opt_timeout(const fps_search_opts* o) { return (o && o->timeout_s > 0) ? o->timeout_s : 2.0; }
 
+// Host result slots [from, k) that no record fills hold -1 (index and distance).
+void fill_unused(int32_t* out_index, int32_t* out_dist, int from, int k) {
+  for (int i = from; i < k; ++i) {
+    out_index[i] = -1;
+    out_dist[i] = -1;
+  }
+}
+
 // Host-IO single search through the workspace staging buffers.
 fps_status search_one_host(Library* L, const uint64_t q[3], int k, int32_t* out_index, int32_t* out_dist,
                            int32_t* out_count, const fps_search_opts* opts, cudaStream_t s) {
   if (L->n == 0 || k == 0) {
+    fill_unused(out_index, out_dist, 0, k);
     *out_count = 0;
     return FPS_OK;
   }
@@ -452,12 +461,13 @@ fps_status search_one_host(Library* L, const uint64_t q[3], int k, int32_t* out_
     cudaGetLastError();
     return FPS_ERR_CUDA;
   }
-  if (launch_scan_single(L->dev, w->io->query, k, w->st, w->cand, w->io->res, w->io->res + k_eff, &w->io->count,
+  // indices in res[0, k), distances in res[k, 2k) (the kernel writes -1 past k_eff)
+  if (launch_scan_single(L->dev, w->io->query, k, w->st, w->cand, w->io->res, w->io->res + k, &w->io->count,
                          &w->io->err, L->num_sms, opt_timeout(opts), s) != cudaSuccess) {
     cudaGetLastError();
     return FPS_ERR_CUDA;
   }
-  size_t bytes = offsetof(HostIO, res) - offsetof(HostIO, err) + 2 * sizeof(int32_t) * k_eff;
+  size_t bytes = offsetof(HostIO, res) - offsetof(HostIO, err) + 2 * sizeof(int32_t) * k;
   if (cudaMemcpyAsync(&w->io_host->err, &w->io->err, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess) {
     cudaGetLastError();
@@ -466,7 +476,8 @@ fps_status search_one_host(Library* L, const uint64_t q[3], int k, int32_t* out_
   if (w->io_host->err) return take_device_error(w, s);
   const int c = w->io_host->count;
   std::memcpy(out_index, w->io_host->res, sizeof(int32_t) * c);
-  std::memcpy(out_dist, w->io_host->res + k_eff, sizeof(int32_t) * c);
+  std::memcpy(out_dist, w->io_host->res + k, sizeof(int32_t) * c);
+  fill_unused(out_index, out_dist, c, k);
   *out_count = c;
   if (opts && opts->stats) {
     opts->stats->queries = 1;
@@ -705,6 +716,7 @@ fps_status finish_batch(Library* L, Workspace* w, const char* hb, const char* db
       out_count[q] = hc[q];
       std::memcpy(out_index + off[q], hi + off[q], sizeof(int32_t) * hc[q]);
       std::memcpy(out_dist + off[q], hd + off[q], sizeof(int32_t) * hc[q]);
+      fill_unused(out_index + off[q], out_dist + off[q], hc[q], k[q]);
     }
   }
   *n_fallback = nf;
@@ -859,6 +871,7 @@ fps_status search_batch_impl(Library* L, const uint64_t* queries, int Q, const i
     out_count[q] = hc[q];
     std::memcpy(out_index + off[q], hi + off[q], sizeof(int32_t) * hc[q]);
     std::memcpy(out_dist + off[q], hd + off[q], sizeof(int32_t) * hc[q]);
+    fill_unused(out_index + off[q], out_dist + off[q], hc[q], k[q]);
   }
   if (opts && opts->stats) {
     opts->stats->queries = Q;
@@ -1111,7 +1124,7 @@ fps_status fps_search(fps_library lib, const char* query166, int k, int32_t* out
   st = search_one_host(L, q, k, out_index, out_dist, &c, nullptr, static_cast<cudaStream_t>(cuda_stream));
   if (st != FPS_OK) return st;
   if (out_cid)
-    for (int i = 0; i < c; ++i) out_cid[i] = L->cids.empty() ? out_index[i] : L->cids[out_index[i]];
+    for (int i = 0; i < k; ++i) out_cid[i] = i >= c ? -1 : (L->cids.empty() ? out_index[i] : L->cids[out_index[i]]);
   *out_count = c;
   return FPS_OK;
 }
@@ -1130,8 +1143,10 @@ fps_status fps_search_packed(fps_library lib, const uint64_t* query, int k, int3
     if (query[2] >> (kBits - 128)) return FPS_ERR_INVALID_ARG;
     return search_one_host(L, query, k, out_index, out_dist, out_count, opts, s);
   }
-  if (L->n == 0 || k == 0) {
-    if (cudaMemsetAsync(out_count, 0, sizeof(int32_t), s) != cudaSuccess) {
+  if (L->n == 0 || k == 0) {   // no records: count 0, every slot -1 (all bytes 0xFF)
+    if (cudaMemsetAsync(out_count, 0, sizeof(int32_t), s) != cudaSuccess ||
+        (k > 0 && (cudaMemsetAsync(out_index, 0xFF, sizeof(int32_t) * k, s) != cudaSuccess ||
+                   cudaMemsetAsync(out_dist, 0xFF, sizeof(int32_t) * k, s) != cudaSuccess))) {
       cudaGetLastError();
       return FPS_ERR_CUDA;
     }
@@ -1220,10 +1235,11 @@ fps_status fps_search_shards(const fps_library* libs, int n_libs, const int64_t*
   Workspace* w = nullptr;
   fps_status st = get_workspace(L0, s, &w);
   if (st != FPS_OK) return st;
-  // device staging: [offsets Q+1][queries Q*3 (host form)][per shard: index, dist (total each), count Q]
+  // device staging: [offsets Q+1][k Q][queries Q*3 (host form)][per shard: index, dist (total each), count Q]
   //                 [merged index, dist, count (host form)]
   Carve cv;
   const size_t d_off = cv.take(sizeof(int64_t) * (Q + 1));
+  const size_t d_k = cv.take(sizeof(int32_t) * Q);
   const size_t d_q = cv.take(dev_io ? 0 : sizeof(uint64_t) * 3 * Q);
   std::vector<size_t> d_si(n_libs), d_sd(n_libs), d_sc(n_libs);
   for (int i = 0; i < n_libs; ++i) {
@@ -1241,6 +1257,7 @@ fps_status fps_search_shards(const fps_library* libs, int n_libs, const int64_t*
   char* db = static_cast<char*>(w->shard_block);
   char* hb = static_cast<char*>(w->shard_host);
   std::memcpy(hb + d_off, out_offsets, sizeof(int64_t) * (Q + 1));
+  std::memcpy(hb + d_k, k, sizeof(int32_t) * Q);
   if (!dev_io) std::memcpy(hb + d_q, queries, sizeof(uint64_t) * 3 * Q);
   if (cudaMemcpyAsync(db, hb, dev_io ? d_q : d_q + sizeof(uint64_t) * 3 * Q, cudaMemcpyHostToDevice, s) !=
       cudaSuccess) {
@@ -1279,7 +1296,8 @@ fps_status fps_search_shards(const fps_library* libs, int n_libs, const int64_t*
   int32_t* mi = dev_io ? out_index : reinterpret_cast<int32_t*>(db + d_mi);
   int32_t* md = dev_io ? out_dist : reinterpret_cast<int32_t*>(db + d_md);
   int32_t* mc = dev_io ? out_count : reinterpret_cast<int32_t*>(db + d_mc);
-  if (launch_shard_merge(sl, Q, reinterpret_cast<const int64_t*>(db + d_off), mi, md, mc, s) != cudaSuccess) {
+  if (launch_shard_merge(sl, Q, reinterpret_cast<const int64_t*>(db + d_off), reinterpret_cast<const int32_t*>(db + d_k),
+                         mi, md, mc, s) != cudaSuccess) {
     cudaGetLastError();
     return FPS_ERR_CUDA;
   }
@@ -1297,8 +1315,13 @@ fps_status fps_search_shards(const fps_library* libs, int n_libs, const int64_t*
       if (st == FPS_OK) st = take_device_error(wi, s);
       if (st != FPS_OK) return st;
     }
-    std::memcpy(out_index, hb + d_mi, sizeof(int32_t) * total);
-    std::memcpy(out_dist, hb + d_md, sizeof(int32_t) * total);
+    // k[q] slots per query (the merge wrote -1 past its count); slots past k stay the caller's
+    const int32_t* hmi = reinterpret_cast<const int32_t*>(hb + d_mi);
+    const int32_t* hmd = reinterpret_cast<const int32_t*>(hb + d_md);
+    for (int q = 0; q < Q; ++q) {
+      std::memcpy(out_index + out_offsets[q], hmi + out_offsets[q], sizeof(int32_t) * k[q]);
+      std::memcpy(out_dist + out_offsets[q], hmd + out_offsets[q], sizeof(int32_t) * k[q]);
+    }
     std::memcpy(out_count, hb + d_mc, sizeof(int32_t) * Q);
   }
   if (opts && opts->stats) {
@@ -1447,8 +1470,8 @@ fps_status fps_cluster_search(fps_library lib, const uint64_t* queries, int Q, i
                          false, s);
   if (st != FPS_OK) return st;
   for (int t = 0; t < best && k > 0; ++t) {
-    std::memcpy(out_index + static_cast<size_t>(t) * k, ti.data() + off[t], sizeof(int32_t) * out_count[t]);
-    std::memcpy(out_dist + static_cast<size_t>(t) * k, td.data() + off[t], sizeof(int32_t) * out_count[t]);
+    std::memcpy(out_index + static_cast<size_t>(t) * k, ti.data() + off[t], sizeof(int32_t) * k);   // -1 past the count
+    std::memcpy(out_dist + static_cast<size_t>(t) * k, td.data() + off[t], sizeof(int32_t) * k);
   }
   return FPS_OK;
 }
@@ -1484,6 +1507,7 @@ fps_status fps_merge_topk(const int32_t* idx, const int32_t* dist, const int64_t
       std::push_heap(heap.begin(), heap.end(), cmp);
     }
   }
+  fill_unused(out_index, out_dist, n, k);
   *out_n = n;
   return FPS_OK;
 }

@@ -149,8 +149,8 @@ struct ShardLists {
   int64_t base[kShardsMax];
 };
 // out_count[q] = entries written for query q (<= off[q+1] - off[q])
-cudaError_t launch_shard_merge(const ShardLists& sl, int Q, const int64_t* off, int32_t* out_idx, int32_t* out_dist,
-                               int32_t* out_count, cudaStream_t s);
+cudaError_t launch_shard_merge(const ShardLists& sl, int Q, const int64_t* off, const int32_t* k, int32_t* out_idx,
+                               int32_t* out_dist, int32_t* out_count, cudaStream_t s);
 // *slot_dev = value, in stream order (slot_dev: device view of pinned host memory)
 cudaError_t launch_progress(int64_t* slot_dev, int64_t value, cudaStream_t s);
 

@@ -771,6 +771,11 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
       if (tid == 0) *out_count = k_eff;
     }
   }
+  // slots past min(k, N), up to k, hold -1
+  for (int i = k_eff + tid; i < k; i += blockDim.x) {
+    out_idx[i] = -1;
+    out_dist[i] = -1;
+  }
   // restore the scan state for the next search on this workspace
   for (int b = tid; b < 168; b += blockDim.x) st->hist[b] = 0u;
   if (tid == 0) {

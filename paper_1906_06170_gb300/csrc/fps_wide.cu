@@ -372,6 +372,11 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
       out_den[i] = static_cast<int32_t>(u);
     }
   }
+  for (int i = nout + tid; i < k; i += blockDim.x) {   // slots past min(k, N), up to k, hold -1
+    out_idx[i] = -1;
+    out_num[i] = -1;
+    out_den[i] = -1;
+  }
   if (tid == 0) {
     *out_count = nout;
     st->thr_key = ~0ull;   // ready for the next search on this state
@@ -621,13 +626,18 @@ fps_status fps_wide_search(fps_wide_library lib, const uint64_t* query, int k, i
   if (!dev_io && (L->n_bits & 63) && (query[W - 1] >> (L->n_bits & 63))) return FPS_ERR_INVALID_ARG;
   WideGuard g(L->device);
   if (!g.ok) return FPS_ERR_CUDA;
-  if (L->dev.n == 0 || k == 0) {
+  if (L->dev.n == 0 || k == 0) {   // no records: count 0, every slot -1
     if (dev_io) {
-      if (cudaMemsetAsync(out_count, 0, sizeof(int32_t), s) != cudaSuccess) {
+      const size_t b = sizeof(int32_t) * k;
+      if (cudaMemsetAsync(out_count, 0, sizeof(int32_t), s) != cudaSuccess ||
+          (k > 0 && (cudaMemsetAsync(out_index, 0xFF, b, s) != cudaSuccess ||
+                     cudaMemsetAsync(out_num, 0xFF, b, s) != cudaSuccess ||
+                     cudaMemsetAsync(out_den, 0xFF, b, s) != cudaSuccess))) {
         cudaGetLastError();
         return FPS_ERR_CUDA;
       }
     } else {
+      for (int i = 0; i < k; ++i) out_index[i] = out_num[i] = out_den[i] = -1;
       *out_count = 0;
     }
     return FPS_OK;
@@ -668,9 +678,9 @@ fps_status fps_wide_search(fps_wide_library lib, const uint64_t* query, int k, i
     return FPS_ERR_CUDA;
   }
   const int c = w->host[3 * FPS_K_MAX];
-  std::memcpy(out_index, w->host, sizeof(int32_t) * c);
-  std::memcpy(out_num, w->host + FPS_K_MAX, sizeof(int32_t) * c);
-  std::memcpy(out_den, w->host + 2 * FPS_K_MAX, sizeof(int32_t) * c);
+  std::memcpy(out_index, w->host, sizeof(int32_t) * k);   // the kernel wrote -1 past c
+  std::memcpy(out_num, w->host + FPS_K_MAX, sizeof(int32_t) * k);
+  std::memcpy(out_den, w->host + 2 * FPS_K_MAX, sizeof(int32_t) * k);
   *out_count = c;
   return FPS_OK;
 }

@@ -19,8 +19,10 @@
 //                 for a singleton or max(a, b) = 0); a clustering's score is
 //                 the sum over queries.
 // Every tie goes to the smaller query index.  All arithmetic is integer, so
-// the chosen count and the medoids equal the oracle's exactly.  The host
-// (fps_host.cpp) runs the rounds and searches the library with the medoids.
+// the chosen count and the medoids equal the oracle's exactly.  The rounds of
+// all counts run together, each kernel covering every count still moving; the
+// host (fps_host.cpp) checks once per round whether any count goes on, then
+// searches the library with the chosen count's medoids.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -104,12 +106,24 @@ __global__ void select_kernel(const int32_t* __restrict__ val, int Q, int mode, 
   }
 }
 
-// lab[i] = the nearest medoid (ties: the one chosen first)
-__global__ void assign_kernel(const int32_t* __restrict__ D, int Q, const int32_t* __restrict__ med, int c,
-                              int32_t* __restrict__ lab) {
+// ------------------------------------------- k-medoids rounds for every count at once
+// Slot s clusters into c_min + s groups.  Each round runs the assignment, the
+// within-cluster row sums and the medoid update of every slot still active;
+// a slot stops when its medoids repeat (its labels then belong to them) or
+// after kClusterIters rounds (its labels are then re-derived from the last
+// medoids), exactly as one count at a time would.
+
+// lab[s][i] = the nearest medoid of slot s (ties: the one chosen first).  final_pass: only
+// the slots that ran out of rounds.
+__global__ void assign_multi_kernel(ClusterRounds r, int final_pass) {
+  const int s = blockIdx.y;
+  const int32_t* st = r.state + 4 * s;
+  if (final_pass ? st[2] == 0 : st[0] == 0) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= Q) return;
-  const int32_t* row = D + static_cast<size_t>(i) * Q;
+  if (i >= r.Q) return;
+  const int c = r.c_min + s;
+  const int32_t* med = r.med + kClusterMaxC * s;
+  const int32_t* row = r.D + static_cast<size_t>(i) * r.Q;
   int bt = 0;
   int32_t bd = row[med[0]];
   for (int t = 1; t < c; ++t) {
@@ -119,21 +133,46 @@ __global__ void assign_kernel(const int32_t* __restrict__ D, int Q, const int32_
       bt = t;
     }
   }
-  lab[i] = bt;
+  r.lab[static_cast<size_t>(s) * r.Q + i] = bt;
 }
 
-// new medoid of every cluster: its member with the smallest cost (ties: smaller index); an empty
-// cluster keeps its medoid.  *changed = 1 if any medoid moved.  One block, one warp per cluster.
-__global__ void medoid_kernel(const int32_t* __restrict__ cost, const int32_t* __restrict__ lab, int Q, int c,
-                              const int32_t* __restrict__ med_old, int32_t* __restrict__ med_new,
-                              int32_t* __restrict__ changed) {
+// cost[s][i] = sum of D[i][j] over the members j of i's cluster in slot s (one warp per row)
+__global__ void rowsum_multi_kernel(ClusterRounds r) {
+  const int s = blockIdx.y;
+  if (r.state[4 * s] == 0) return;
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (i >= r.Q) return;
+  const int32_t* row = r.D + static_cast<size_t>(i) * r.Q;
+  const int32_t* lab = r.lab + static_cast<size_t>(s) * r.Q;
+  const int li = lab[i];
+  int32_t sum = 0;
+  for (int j = lane; j < r.Q; j += 32)
+    if (lab[j] == li) sum += row[j];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(kFull, sum, o);
+  if (lane == 0) r.cost[static_cast<size_t>(s) * r.Q + i] = sum;
+}
+
+// One block per slot: every cluster's member with the smallest cost (ties: smaller index;
+// an empty cluster keeps its medoid), then the slot's state for the next round.
+// any_active[round] = 1 if some slot goes on.
+__global__ void medoid_multi_kernel(ClusterRounds r, int round) {
+  const int s = blockIdx.x;
+  int32_t* st = r.state + 4 * s;
+  if (st[0] == 0) return;
+  const int c = r.c_min + s;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  __shared__ int any;
-  if (threadIdx.x == 0) any = 0;
+  const int32_t* lab = r.lab + static_cast<size_t>(s) * r.Q;
+  const int32_t* cost = r.cost + static_cast<size_t>(s) * r.Q;
+  int32_t* med = r.med + kClusterMaxC * s;
+  __shared__ int32_t nm[kClusterMaxC];
+  __shared__ int changed;
+  if (threadIdx.x == 0) changed = 0;
   __syncthreads();
   for (int t = warp; t < c; t += blockDim.x >> 5) {
     long long mine = LLONG_MAX;
-    for (int i = lane; i < Q; i += 32)
+    for (int i = lane; i < r.Q; i += 32)
       if (lab[i] == t) {
         const long long packed = (static_cast<long long>(cost[i]) << 32) | static_cast<long long>(i);
         mine = packed < mine ? packed : mine;
@@ -144,13 +183,25 @@ __global__ void medoid_kernel(const int32_t* __restrict__ cost, const int32_t* _
       mine = other < mine ? other : mine;
     }
     if (lane == 0) {
-      const int32_t m = mine == LLONG_MAX ? med_old[t] : static_cast<int32_t>(mine & 0xFFFFFFFFll);
-      med_new[t] = m;
-      if (m != med_old[t]) atomicExch(&any, 1);
+      const int32_t m = mine == LLONG_MAX ? med[t] : static_cast<int32_t>(mine & 0xFFFFFFFFll);
+      nm[t] = m;
+      if (m != med[t]) atomicExch(&changed, 1);
     }
   }
   __syncthreads();
-  if (threadIdx.x == 0) *changed = any;
+  if (threadIdx.x == 0) {
+    if (!changed) {
+      st[0] = 0;                          // the medoids repeat: the labels belong to them
+    } else {
+      for (int t = 0; t < c; ++t) med[t] = nm[t];
+      if (++st[1] == kClusterIters) {
+        st[0] = 0;                        // out of rounds: labels of the new medoids follow
+        st[2] = 1;
+      } else {
+        r.any_active[round] = 1;
+      }
+    }
+  }
 }
 
 __global__ void sizes_kernel(const int32_t* __restrict__ lab, int Q, int c, int32_t* __restrict__ sizes) {
@@ -163,25 +214,27 @@ __global__ void sizes_kernel(const int32_t* __restrict__ lab, int Q, int c, int3
 }
 
 // One warp per query: per-cluster sums of its row, then floor(s * 2^32) added to *score.
-__global__ void silhouette_kernel(const int32_t* __restrict__ D, int Q, const int32_t* __restrict__ lab, int c,
-                                  const int32_t* __restrict__ sizes, unsigned long long* __restrict__ score) {
-  const int lane = threadIdx.x & 31;
-  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (i >= Q) return;
+// Each lane adds its elements into its own column of shared counters indexed by the
+// element's cluster (one add per element, no bank conflicts), then the columns are summed.
+constexpr int kSilWarps = 8;
+__global__ void __launch_bounds__(32 * kSilWarps)
+    silhouette_kernel(const int32_t* __restrict__ D, int Q, const int32_t* __restrict__ lab, int c,
+                      const int32_t* __restrict__ sizes, unsigned long long* __restrict__ score) {
+  __shared__ int32_t acc[kSilWarps][kClusterMaxC][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int i = blockIdx.x * kSilWarps + w;
+  if (i >= Q) return;   // whole warps only: the block has no block-wide barrier
+#pragma unroll
+  for (int t = 0; t < kClusterMaxC; ++t) acc[w][t][lane] = 0;
   const int32_t* row = D + static_cast<size_t>(i) * Q;
+  for (int j = lane; j < Q; j += 32) acc[w][lab[j]][lane] += row[j];
+  __syncwarp();
+  int32_t mine = 0;   // lane t: the sum over cluster t
+  if (lane < kClusterMaxC)
+    for (int l = 0; l < 32; ++l) mine += acc[w][lane][l];
   int32_t sums[kClusterMaxC];
 #pragma unroll
-  for (int t = 0; t < kClusterMaxC; ++t) sums[t] = 0;
-  for (int j = lane; j < Q; j += 32) {
-    const int32_t d = row[j];
-    const int lj = lab[j];
-#pragma unroll
-    for (int t = 0; t < kClusterMaxC; ++t) sums[t] += (lj == t) ? d : 0;
-  }
-#pragma unroll
-  for (int t = 0; t < kClusterMaxC; ++t)
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) sums[t] += __shfl_xor_sync(kFull, sums[t], o);
+  for (int t = 0; t < kClusterMaxC; ++t) sums[t] = __shfl_sync(kFull, mine, t);
   if (lane != 0) return;
   const int A = lab[i];
   long long s_fixed = 0;
@@ -233,14 +286,21 @@ cudaError_t cluster_select(const int32_t* val, int Q, bool largest, const int32_
   return cudaGetLastError();
 }
 
-cudaError_t cluster_assign(const int32_t* D, int Q, const int32_t* med, int c, int32_t* lab, cudaStream_t s) {
-  assign_kernel<<<(Q + 255) / 256, 256, 0, s>>>(D, Q, med, c, lab);
+cudaError_t cluster_round(const ClusterRounds& r, int round, cudaStream_t s) {
+  if (r.n_slots <= 0) return cudaSuccess;
+  assign_multi_kernel<<<dim3((r.Q + 255) / 256, r.n_slots), 256, 0, s>>>(r, 0);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  rowsum_multi_kernel<<<dim3((r.Q + 7) / 8, r.n_slots), 256, 0, s>>>(r);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  medoid_multi_kernel<<<r.n_slots, 512, 0, s>>>(r, round);
   return cudaGetLastError();
 }
 
-cudaError_t cluster_medoids(const int32_t* cost, const int32_t* lab, int Q, int c, const int32_t* med_old,
-                            int32_t* med_new, int32_t* changed, cudaStream_t s) {
-  medoid_kernel<<<1, 512, 0, s>>>(cost, lab, Q, c, med_old, med_new, changed);
+cudaError_t cluster_final_assign(const ClusterRounds& r, cudaStream_t s) {
+  if (r.n_slots <= 0) return cudaSuccess;
+  assign_multi_kernel<<<dim3((r.Q + 255) / 256, r.n_slots), 256, 0, s>>>(r, 1);
   return cudaGetLastError();
 }
 
@@ -249,7 +309,7 @@ cudaError_t cluster_silhouette(const int32_t* D, int Q, const int32_t* lab, int 
   sizes_kernel<<<1, 1024, 0, s>>>(lab, Q, c, sizes);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  silhouette_kernel<<<(Q + 7) / 8, 256, 0, s>>>(D, Q, lab, c, sizes, score);
+  silhouette_kernel<<<(Q + kSilWarps - 1) / kSilWarps, 32 * kSilWarps, 0, s>>>(D, Q, lab, c, sizes, score);
   return cudaGetLastError();
 }
 

@@ -1351,22 +1351,24 @@ fps_status fps_cluster_search(fps_library lib, const uint64_t* queries, int Q, i
   if (!g.ok) return FPS_ERR_CUDA;
   const int c_hi = std::min(c_max, Q - 1);
   const int n_c = c_max - c_min + 1;
-  // device scratch: queries, D, row sums, near, cost, label per count, medoid per count, small words
+  // device scratch: queries, D, row sums, per count: labels, costs, medoids, round state;
+  // seeds, round flags, sizes, scores
   Carve cv;
   const size_t d_q = cv.take(sizeof(uint64_t) * 3 * Q);
   const size_t d_D = cv.take(sizeof(int32_t) * static_cast<size_t>(Q) * Q);
   const size_t d_rs = cv.take(sizeof(int32_t) * Q);
-  const size_t d_cost = cv.take(sizeof(int32_t) * Q);
+  const size_t d_cost = cv.take(sizeof(int32_t) * static_cast<size_t>(Q) * n_c);
   const size_t d_lab = cv.take(sizeof(int32_t) * static_cast<size_t>(Q) * n_c);
   const size_t d_seed = cv.take(sizeof(int32_t) * kClusterMaxC);
   const size_t d_med = cv.take(sizeof(int32_t) * kClusterMaxC * n_c);
-  const size_t d_tmp = cv.take(sizeof(int32_t) * kClusterMaxC);
-  const size_t d_flag = cv.take(sizeof(int32_t) * 2);
+  const size_t d_state = cv.take(sizeof(int32_t) * 4 * n_c);
+  const size_t d_any = cv.take(sizeof(int32_t) * kClusterIters);
   const size_t d_sizes = cv.take(sizeof(int32_t) * kClusterMaxC);
   const size_t d_score = cv.take(sizeof(unsigned long long) * n_c);
   char* db = nullptr;
-  int32_t* hflag = nullptr;
-  if (cudaMalloc(&db, cv.at) != cudaSuccess || cudaMallocHost(&hflag, sizeof(int32_t) * 2) != cudaSuccess) {
+  int32_t* hflag = nullptr;   // pinned: the round state to upload, then one round flag at a time
+  const size_t h_words = 4 * static_cast<size_t>(n_c);
+  if (cudaMalloc(&db, cv.at) != cudaSuccess || cudaMallocHost(&hflag, sizeof(int32_t) * h_words) != cudaSuccess) {
     cudaGetLastError();
     if (db) cudaFree(db);
     return FPS_ERR_CUDA;
@@ -1380,10 +1382,7 @@ fps_status fps_cluster_search(fps_library lib, const uint64_t* queries, int Q, i
   };
   int32_t* D = reinterpret_cast<int32_t*>(db + d_D);
   int32_t* rs = reinterpret_cast<int32_t*>(db + d_rs);
-  int32_t* cost = reinterpret_cast<int32_t*>(db + d_cost);
   int32_t* seed = reinterpret_cast<int32_t*>(db + d_seed);
-  int32_t* tmp = reinterpret_cast<int32_t*>(db + d_tmp);
-  int32_t* flag = reinterpret_cast<int32_t*>(db + d_flag);
   int32_t* sizes = reinterpret_cast<int32_t*>(db + d_sizes);
   unsigned long long* score = reinterpret_cast<unsigned long long*>(db + d_score);
   if (cudaMemcpyAsync(db + d_q, queries, sizeof(uint64_t) * 3 * Q, cudaMemcpyHostToDevice, s) != cudaSuccess ||
@@ -1399,26 +1398,32 @@ fps_status fps_cluster_search(fps_library lib, const uint64_t* queries, int Q, i
         cluster_select(rs, Q, true, seed, t, nullptr, 0, seed + t, s) != cudaSuccess)
       return fail(FPS_ERR_CUDA);
   }
-  for (int c = c_min; c <= c_hi; ++c) {
-    const int slot = c - c_min;
-    int32_t* med = reinterpret_cast<int32_t*>(db + d_med) + kClusterMaxC * slot;
-    int32_t* lab = reinterpret_cast<int32_t*>(db + d_lab) + static_cast<size_t>(Q) * slot;
-    if (cudaMemcpyAsync(med, seed, sizeof(int32_t) * c, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+  // k-medoids for every count at once: one host check per round (some count still moving)
+  const int n_live = c_hi >= c_min ? c_hi - c_min + 1 : 0;
+  ClusterRounds rr{D, Q, c_min, n_live, reinterpret_cast<int32_t*>(db + d_med), reinterpret_cast<int32_t*>(db + d_lab),
+                   reinterpret_cast<int32_t*>(db + d_cost), reinterpret_cast<int32_t*>(db + d_state),
+                   reinterpret_cast<int32_t*>(db + d_any)};
+  for (size_t w = 0; w < h_words; ++w) hflag[w] = 0;
+  for (int t = 0; t < n_live; ++t) hflag[4 * t] = 1;   // active, no rounds yet
+  if (n_live > 0 &&
+      (cudaMemcpyAsync(rr.state, hflag, sizeof(int32_t) * 4 * n_live, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+       cudaMemsetAsync(rr.any_active, 0, sizeof(int32_t) * kClusterIters, s) != cudaSuccess))
+    return fail(FPS_ERR_CUDA);
+  for (int t = 0; t < n_live; ++t)   // slot t starts from the first c_min + t seeds
+    if (cudaMemcpyAsync(rr.med + kClusterMaxC * t, seed, sizeof(int32_t) * (c_min + t), cudaMemcpyDeviceToDevice,
+                        s) != cudaSuccess)
       return fail(FPS_ERR_CUDA);
-    for (int it = 0; it < kClusterIters; ++it) {
-      if (cluster_assign(D, Q, med, c, lab, s) != cudaSuccess || cluster_rowsum(D, Q, lab, cost, s) != cudaSuccess ||
-          cluster_medoids(cost, lab, Q, c, med, tmp, flag, s) != cudaSuccess ||
-          cudaMemcpyAsync(hflag, flag, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-          cudaStreamSynchronize(s) != cudaSuccess)
-        return fail(FPS_ERR_CUDA);
-      if (!hflag[0]) break;   // the medoids repeat: lab already belongs to them
-      if (cudaMemcpyAsync(med, tmp, sizeof(int32_t) * c, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-        return fail(FPS_ERR_CUDA);
-      if (it + 1 == kClusterIters && cluster_assign(D, Q, med, c, lab, s) != cudaSuccess)
-        return fail(FPS_ERR_CUDA);
-    }
-    if (cluster_silhouette(D, Q, lab, c, sizes, score + slot, s) != cudaSuccess) return fail(FPS_ERR_CUDA);
+  for (int round = 0; round < kClusterIters && n_live > 0; ++round) {
+    if (cluster_round(rr, round, s) != cudaSuccess ||
+        cudaMemcpyAsync(hflag, rr.any_active + round, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return fail(FPS_ERR_CUDA);
+    if (!hflag[0]) break;   // every count's medoids repeat, or its rounds are used up
   }
+  if (cluster_final_assign(rr, s) != cudaSuccess) return fail(FPS_ERR_CUDA);
+  for (int t = 0; t < n_live; ++t)
+    if (cluster_silhouette(D, Q, rr.lab + static_cast<size_t>(Q) * t, c_min + t, sizes, score + t, s) != cudaSuccess)
+      return fail(FPS_ERR_CUDA);
   std::vector<unsigned long long> sc(n_c, 0ull);
   if (cudaMemcpyAsync(sc.data(), score, sizeof(unsigned long long) * n_c, cudaMemcpyDeviceToHost, s) !=
           cudaSuccess ||

@@ -164,9 +164,22 @@ cudaError_t cluster_near(const int32_t* D, int Q, const int32_t* m, bool first, 
 // *out = argmin (or argmax) of val over the queries not in ex[0..n_ex) (lab == nullptr) or with lab == want
 cudaError_t cluster_select(const int32_t* val, int Q, bool largest, const int32_t* ex, int n_ex, const int32_t* lab,
                            int want, int32_t* out, cudaStream_t s);
-cudaError_t cluster_assign(const int32_t* D, int Q, const int32_t* med, int c, int32_t* lab, cudaStream_t s);
-cudaError_t cluster_medoids(const int32_t* cost, const int32_t* lab, int Q, int c, const int32_t* med_old,
-                            int32_t* med_new, int32_t* changed, cudaStream_t s);
+// k-medoids rounds for every cluster count at once (slot s: c_min + s clusters).
+// state[4 s] = {active, rounds done, needs a final assignment, unused}; any_active has
+// kClusterIters words, word r set when some slot goes on after round r.
+struct ClusterRounds {
+  const int32_t* D;
+  int Q;
+  int c_min;
+  int n_slots;
+  int32_t* med;          // [n_slots][kClusterMaxC], starts as the seeds
+  int32_t* lab;          // [n_slots][Q]
+  int32_t* cost;         // [n_slots][Q]
+  int32_t* state;        // [n_slots][4]
+  int32_t* any_active;   // [kClusterIters]
+};
+cudaError_t cluster_round(const ClusterRounds& r, int round, cudaStream_t s);
+cudaError_t cluster_final_assign(const ClusterRounds& r, cudaStream_t s);
 // *score += sum_i floor(s_i 2^32) (two's complement in 64 bits)
 cudaError_t cluster_silhouette(const int32_t* D, int Q, const int32_t* lab, int c, int32_t* sizes,
                                unsigned long long* score, cudaStream_t s);

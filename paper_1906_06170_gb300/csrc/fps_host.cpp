@@ -199,6 +199,8 @@ void free_library(Library* L) {
     if (w->batch_host) cudaFreeHost(w->batch_host);
     if (w->shard_block) cudaFree(w->shard_block);
     if (w->shard_host) cudaFreeHost(w->shard_host);
+    if (w->cluster_block) cudaFree(w->cluster_block);
+    if (w->cluster_host) cudaFreeHost(w->cluster_host);
     delete w;
   }
   L->ws.clear();
@@ -1365,19 +1367,18 @@ fps_status fps_cluster_search(fps_library lib, const uint64_t* queries, int Q, i
   const size_t d_any = cv.take(sizeof(int32_t) * kClusterIters);
   const size_t d_sizes = cv.take(sizeof(int32_t) * kClusterMaxC);
   const size_t d_score = cv.take(sizeof(unsigned long long) * n_c);
-  char* db = nullptr;
-  int32_t* hflag = nullptr;   // pinned: the round state to upload, then one round flag at a time
-  const size_t h_words = 4 * static_cast<size_t>(n_c);
-  if (cudaMalloc(&db, cv.at) != cudaSuccess || cudaMallocHost(&hflag, sizeof(int32_t) * h_words) != cudaSuccess) {
-    cudaGetLastError();
-    if (db) cudaFree(db);
-    return FPS_ERR_CUDA;
-  }
+  // the scratch lives in the stream's workspace and only grows (no allocation per call)
+  const size_t h_words = 4 * static_cast<size_t>(n_c);   // pinned: round state up, one round flag down
+  Workspace* w = nullptr;
+  st = get_workspace(L, s, &w);
+  if (st == FPS_OK) st = grow_block(&w->cluster_block, &w->cluster_bytes, cv.at, false);
+  if (st == FPS_OK) st = grow_block(&w->cluster_host, &w->cluster_host_bytes, sizeof(int32_t) * h_words, true);
+  if (st != FPS_OK) return st;
+  char* db = static_cast<char*>(w->cluster_block);
+  int32_t* hflag = static_cast<int32_t*>(w->cluster_host);
   auto fail = [&](fps_status code) {
     cudaGetLastError();
     cudaStreamSynchronize(s);
-    cudaFree(db);
-    cudaFreeHost(hflag);
     return code;
   };
   int32_t* D = reinterpret_cast<int32_t*>(db + d_D);
@@ -1403,7 +1404,7 @@ fps_status fps_cluster_search(fps_library lib, const uint64_t* queries, int Q, i
   ClusterRounds rr{D, Q, c_min, n_live, reinterpret_cast<int32_t*>(db + d_med), reinterpret_cast<int32_t*>(db + d_lab),
                    reinterpret_cast<int32_t*>(db + d_cost), reinterpret_cast<int32_t*>(db + d_state),
                    reinterpret_cast<int32_t*>(db + d_any)};
-  for (size_t w = 0; w < h_words; ++w) hflag[w] = 0;
+  for (size_t x = 0; x < h_words; ++x) hflag[x] = 0;
   for (int t = 0; t < n_live; ++t) hflag[4 * t] = 1;   // active, no rounds yet
   if (n_live > 0 &&
       (cudaMemcpyAsync(rr.state, hflag, sizeof(int32_t) * 4 * n_live, cudaMemcpyHostToDevice, s) != cudaSuccess ||
@@ -1456,8 +1457,6 @@ fps_status fps_cluster_search(fps_library lib, const uint64_t* queries, int Q, i
         cudaStreamSynchronize(s) != cudaSuccess)
       return fail(FPS_ERR_CUDA);
   }
-  cudaFree(db);
-  cudaFreeHost(hflag);
   *out_c = best;
   for (int t = 0; t < best; ++t) out_medoids[t] = med_h[t];
   // every cluster searched with its medoid (one after another through the single-query scan)

@@ -88,6 +88,10 @@ struct Workspace {
   size_t shard_bytes = 0;
   void* shard_host = nullptr;
   size_t shard_host_bytes = 0;
+  void* cluster_block = nullptr;    // batch clustering scratch (device), grown on demand
+  size_t cluster_bytes = 0;
+  void* cluster_host = nullptr;     // its pinned round-state words
+  size_t cluster_host_bytes = 0;
 };
 
 struct Library {

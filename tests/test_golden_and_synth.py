@@ -46,6 +46,46 @@ def test_seeded_topk_fixture():
         assert list(zip(idx.tolist(), dist.tolist())) == pairs
 
 
+def test_seeded_wide_fixture():
+    """n-bit extension: 1024-bit top-20, Manhattan and Tanimoto (tests/golden/make_golden.py)."""
+    want = {}
+    with open(os.path.join(GOLD, "wide_seed21_n3000.txt")) as f:
+        for line in f:
+            if line.startswith("#"):
+                continue
+            m, q, r, i, a, b = map(int, line.split())
+            want.setdefault((m, q), []).append((i, a, b))
+    assert sorted(want) == [(0, 0), (0, 1), (1, 0), (1, 1)]
+    text = synth.wide_text(3000, 1024, 21)
+    queries = synth.wide_to_strings(synth.wide_packed(2, 1024, 1021), 1024)
+    for (m, q), rows in want.items():
+        idx, num, den = oracle.wide_topk(text, 1024, queries[q], 20, m)
+        assert list(zip(idx.tolist(), num.tolist(), den.tolist())) == rows
+
+
+def test_seeded_cluster_fixture():
+    """Batch clustering search: scores per count, the chosen count, medoids and labels."""
+    from oracle import cluster
+
+    scores, best, med, lab = {}, None, None, None
+    with open(os.path.join(GOLD, "cluster_seed1400.txt")) as f:
+        for line in f:
+            if line.startswith("#"):
+                continue
+            key, *vals = line.split()
+            if key == "score":
+                scores[int(vals[0])] = int(vals[1])
+            elif key == "best":
+                best = int(vals[0])
+            elif key == "medoids":
+                med = [int(v) for v in vals]
+            elif key == "labels":
+                lab = [int(v) for v in vals]
+    res = cluster.cluster_batch(synth.packed_to_strings(synth.packed(120, 1400)), 2, 6)
+    assert res["scores"] == scores and res["c"] == best
+    assert [int(m) for m in res["medoids"]] == med and res["labels"].tolist() == lab
+
+
 def test_generator_is_thread_count_independent_and_consistent():
     a = synth.packed(50000, 3, threads=1)
     b = synth.packed(50000, 3, threads=7)

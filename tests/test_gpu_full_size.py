@@ -140,3 +140,19 @@ def test_learned_path_full_size(full):
         got = run_batch(fps, lib, qs, ks, fps.FPS_PATH_LEARNED, tau=tau)
         for q, ((gi, gd), (wi, wd)) in enumerate(zip(got, ref)):
             assert np.array_equal(gi, wi) and np.array_equal(gd, wd), (name, q)
+
+
+def test_largest_k_full_size(full):
+    """k = FPS_K_MAX (1920: the single-query scan's 8-warp configuration, the largest candidate regions
+    of the batched paths) at full size: every exact path equals the brute force."""
+    fps, lib, packed, raw = full
+    k = 1920
+    qs = np.concatenate([synth.packed(2, 1005), synth.packed_at([12345], 0)])
+    ks = np.full(len(qs), k, np.int32)
+    want = brute_topk(raw, qs, k)
+    for path in (fps.FPS_PATH_POPC, fps.FPS_PATH_POPC_BATCH, fps.FPS_PATH_TC_FP8):
+        res = run_batch(fps, lib, qs, ks, path)
+        well_formed(res, ks)
+        for q, (gi, gd) in enumerate(res):
+            assert np.array_equal((gd.astype(np.int64) << 32) | gi, want[q, :k]), (path, q)
+    oracle_distances_agree(packed, qs[0], *res[0])

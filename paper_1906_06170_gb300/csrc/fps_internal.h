@@ -159,6 +159,11 @@ cudaError_t launch_shard_merge(const ShardLists& sl, int Q, const int64_t* off, 
 cudaError_t launch_progress(int64_t* slot_dev, int64_t value, cudaStream_t s);
 
 // ---- batch clustering (fps_cluster.cu); every tie goes to the smaller query index
+// A kernel whose bounded wait ran out still waits, this long at least, for its own bulk
+// copies and MMAs in flight before it leaves (they complete in microseconds; a caller's
+// short timeout must not let a CTA exit or free TMEM under them).
+constexpr uint64_t kDrainNs = 1000000000ull;
+
 constexpr int kClusterMaxC = 16;    // largest cluster count
 constexpr int kClusterIters = 30;   // k-medoids rounds at most
 cudaError_t cluster_qdist(const uint64_t* q, int Q, int32_t* D, cudaStream_t s);            // Q x Q distances

@@ -586,7 +586,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
     if (lane == 0) atomicOr(err, DEVERR_TIMEOUT);
     // items fail_j .. n_issued-1 are the copies not yet consumed; each is the
     // next phase of its stage, so waiting on that phase is well defined
-    const uint64_t drain_deadline = global_ns() + timeout_ns;
+    const uint64_t drain_deadline = global_ns() + (timeout_ns > kDrainNs ? timeout_ns : kDrainNs);
     for (int j = fail_j; j < n_issued; ++j)
       mbar_wait_bounded(&bars[j % kStages], static_cast<uint32_t>((j / kStages) & 1), drain_deadline);
   }

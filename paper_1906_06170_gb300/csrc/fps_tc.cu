@@ -400,6 +400,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_after();
   const uint32_t tmem = S.tmem_base;
   const uint64_t deadline = timeout_ns;   // per wait
+  const uint64_t drain = timeout_ns > kDrainNs ? timeout_ns : kDrainNs;   // own copies / MMAs in flight
   bool ok = true;
 
   if (warp == 0) {
@@ -439,13 +440,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int s = 0; s < kBStages; ++s) {
         if (bn > static_cast<uint32_t>(s)) {
           uint32_t last_use = (bn - 1 - s) / kBStages;
-          mbar_wait(&S.b_full[s], last_use & 1, timeout_ns);
+          mbar_wait(&S.b_full[s], last_use & 1, drain);
         }
       }
       for (int a = 0; a < 2; ++a) {
         if (na > static_cast<uint32_t>(a)) {
           uint32_t last_use = (na - 1 - a) / 2;
-          mbar_wait(&S.a_full[a], last_use & 1, timeout_ns);
+          mbar_wait(&S.a_full[a], last_use & 1, drain);
         }
       }
       if (!ok) atomicOr(b.err, DEVERR_TIMEOUT);
@@ -490,7 +491,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!ok) atomicOr(b.err, DEVERR_TIMEOUT);
       // all MMAs issued by this thread complete before the final barrier
       mma_commit(&S.fin);
-      mbar_wait(&S.fin, 0, timeout_ns);
+      mbar_wait(&S.fin, 0, drain);
     }
   } else if (warp < kFlushWarp0) {
     // -------------------------------------------------------------- epilogue

@@ -4,8 +4,9 @@
  * The paper (Sec. 4.3, Fig. 3) searches a library of MACCS-166 fingerprints
  * for the molecules closest to a target: Manhattan distance over the 166
  * 0/1 keys, every library row paired with its distance, all pairs sorted
- * ascending, first k returned with their PubChem CIDs ("Input: target
- * MACCS166, library file F ... Output: CID ... and distance").  Here the
+ * ascending, first k returned with their PubChem CIDs (Fig. 3: the inputs are
+ * the target's MACCS-166 keys and the library file, the output each hit's CID
+ * with its distance).  Here the
  * library is parsed once, packed to 24-byte records and kept in GPU memory;
  * each search is an exhaustive scan plus an exact top-k on the GPU.
  *
@@ -71,9 +72,10 @@ typedef struct fps_library_s* fps_library;
  * Exactly one library source must be given: a file path, an in-memory text
  * buffer, or already-packed records.
  *
- * Text format (Fig. 3 step 1, "obtain all the molecules from F, construct CID,
- * matrix A"): one molecule per line, either 166 '0'/'1' characters or
- * "<cid><sep><166 characters>" with sep a space, tab or comma and cid a
+ * Text format (Fig. 3 step 1: every molecule of the library file is read and
+ * gives one row of the 0/1 matrix and one CID): one molecule per line,
+ * either 166 '0'/'1' characters or "<cid><sep><166 characters>" with sep a
+ * space, tab or comma and cid a
  * non-negative decimal integer.  A trailing '\r' is dropped; the final line
  * may lack its '\n'.  Any other line -- including an empty line before the
  * end -- fails the load with FPS_ERR_PARSE and its 1-based number in
@@ -103,7 +105,10 @@ typedef struct {
 /* Parse (or take) the library, pack it, lay it out by popcount bucket and copy it to the device. */
 fps_status fps_library_load(const fps_load_desc* desc, fps_library* out);
 
-/* Release a library and all device memory it owns.  NULL is accepted (no-op). */
+/* Release a library and all device memory it owns.  NULL is accepted (no-op).
+ * The paper keeps no resident state (it re-reads the library file for every
+ * search, Sec. 2.2); this is the end of the resident library's lifetime that
+ * loading once begins. */
 fps_status fps_release(fps_library lib);
 
 typedef struct {
@@ -174,6 +179,10 @@ fps_status fps_search_packed(fps_library lib, const uint64_t* query, int k, int3
                              int32_t* out_count, const fps_search_opts* opts, void* cuda_stream);
 
 /*
+ * Batched search.  The paper searches one target at a time (Fig. 3) and lists
+ * batch processing of query molecules only for its clustering search
+ * (Sec. 4.4); this entry point runs Q independent Fig. 3 searches in one
+ * call, each with the result of its own single search.
  * Q queries (Q x FPS_WORDS packed words) with per-query k[q].  Results of
  * query q go to out_index/out_dist[out_offsets[q] .. out_offsets[q] + k[q]),
  * out_offsets holding Q + 1 entries (out_offsets[q+1] - out_offsets[q] >= k[q]);
@@ -206,7 +215,11 @@ fps_status fps_search_batch(fps_library lib, const uint64_t* queries, int Q, con
  * All calls on a device share the array: calls that may overlap on the GPU
  * (different streams without ordering between them) race and give wrong
  * results; order them on one stream.  Each call clears the scratch it needs.
- * A device-side failure (a bounded wait that ran out) leaves *out_count = -1.
+ * With no records (or k = 0) *out_count = 0 and, as on every path, the k
+ * result slots hold -1.  Each device-side wait is bounded by 2 s (the
+ * environment variable FPS_NOALLOC_TIMEOUT_NS, read on every call, replaces
+ * that bound; tests use it to make a wait run out).  A device-side failure (a
+ * bounded wait that ran out) leaves *out_count = -1.
  */
 #define FPS_NOALLOC_K_MAX 128
 fps_status fps_search_noalloc(fps_library lib, const uint64_t* query, int k, int32_t* out_index, int32_t* out_dist,

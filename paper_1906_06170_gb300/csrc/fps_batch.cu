@@ -431,13 +431,9 @@ cudaError_t batch_scan_popc(const DevLib& lib, const BatchDev& b, int num_sms, u
 cudaError_t batch_select(const DevLib& lib, const BatchDev& b, cudaStream_t s) {
   if (b.Q == 0) return cudaSuccess;
   const size_t smem = (kSelFin + kSelTies) * sizeof(unsigned long long);
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(batch_select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  static std::atomic<uint64_t> configured{0};
+  cudaError_t e = smem_attr_once(batch_select_kernel, smem, &configured);
+  if (e != cudaSuccess) return e;
   batch_select_kernel<<<b.Q, kSelThreads, smem, s>>>(lib, b);
   return cudaGetLastError();
 }

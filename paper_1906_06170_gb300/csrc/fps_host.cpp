@@ -1,9 +1,9 @@
 // Host side of the C ABI: library parsing/packing, popcount-bucketed layout,
 // device residency, per-stream workspaces and the search entry points.
 //
-// Paper: Fig. 3 step 1 ("obtain all the molecules from F, construct CID,
-// matrix A") becomes a one-time parse of the library text into packed
-// 24-byte records that stay in GPU memory; step 2 (the target's vector B)
+// Paper: Fig. 3 step 1 (read every molecule of the library file, build the
+// CID column and the 0/1 matrix) becomes a one-time parse of the library text
+// into packed 24-byte records that stay in GPU memory; step 2 (the target's vector B)
 // becomes fps_pack_query; steps 3-6 run on the GPU (fps_scan.cu).
 #include <cuda_runtime.h>
 
@@ -548,7 +548,10 @@ fps_status batch_sequential(Library* L, Workspace* w, const uint64_t* dq, int Q,
                             int32_t* di, int32_t* dd, int32_t* dc, double tmo, cudaStream_t s) {
   for (int q = 0; q < Q; ++q) {   // empty results first, so the scan launches stay adjacent
     if (k[q] == 0 || L->n == 0) {
-      if (cudaMemsetAsync(dc + q, 0, sizeof(int32_t), s) != cudaSuccess) {
+      // count 0; with no records every slot up to k holds -1 (all bytes 0xFF)
+      if (cudaMemsetAsync(dc + q, 0, sizeof(int32_t), s) != cudaSuccess ||
+          (k[q] > 0 && (cudaMemsetAsync(di + off[q], 0xFF, sizeof(int32_t) * k[q], s) != cudaSuccess ||
+                        cudaMemsetAsync(dd + off[q], 0xFF, sizeof(int32_t) * k[q], s) != cudaSuccess))) {
         cudaGetLastError();
         return FPS_ERR_CUDA;
       }

@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstddef>
 #include <cstdint>
 #include <map>
@@ -21,6 +22,21 @@ constexpr int kTileBytes = kTile * kWords * 8;
 constexpr int kBucketAlign = 256;      // every popcount bucket starts on a 256-record boundary
 constexpr int kNumBuckets = kBits + 1; // popcounts 0..166
 constexpr int kKMax = FPS_K_MAX;
+
+// A kernel's dynamic shared memory limit is an attribute of the function in each
+// device's context, so it is set once per device: bit d of *done records device d.
+// Threads racing on a device's first launch both set it, which is harmless.
+template <typename F>
+cudaError_t smem_attr_once(F* kernel, size_t bytes, std::atomic<uint64_t>* done) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const uint64_t bit = dev >= 0 && dev < 64 ? 1ull << dev : 0ull;
+  if (bit != 0 && (done->load(std::memory_order_acquire) & bit) != 0) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes));
+  if (e == cudaSuccess && bit != 0) done->fetch_or(bit, std::memory_order_release);
+  return e;
+}
 
 // Device view of a resident library, passed to kernels by value.
 //   words:    [n_tiles][3][kTile] uint64, word-major inside a tile, so a warp's

@@ -32,6 +32,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstdlib>
 
 #include "fps_internal.h"
 
@@ -800,14 +801,8 @@ __global__ void scan_state_init_kernel(ScanState* st) {
 
 template <int WARPS, int CAP>
 cudaError_t configure_cfg() {
-  static bool configured = false;  // attribute set once per process (idempotent)
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(scan_single_kernel<WARPS, CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(Smem<WARPS, CAP>::total));
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
-  return cudaSuccess;
+  static std::atomic<uint64_t> configured{0};   // one per instantiation, a bit per device
+  return smem_attr_once(scan_single_kernel<WARPS, CAP>, Smem<WARPS, CAP>::total, &configured);
 }
 
 template <int WARPS, int CAP>
@@ -936,6 +931,7 @@ namespace {
 
 constexpr int kNoAllocMaxSms = 160;                      // largest grid the array can serve
 constexpr int kNoAllocKMax = kSmallCap - kTile;          // 128: the shared-buffer configuration
+static_assert(kNoAllocKMax == FPS_NOALLOC_K_MAX, "the enforced k limit is the one the header states");
 constexpr size_t kNoAllocStateBytes = (sizeof(ScanState) + 255) / 256 * 256;
 constexpr size_t kNoAllocErrBytes = 256;
 constexpr size_t kNoAllocCandKeys = static_cast<size_t>(kNoAllocMaxSms) * kSmallWarps * kNoAllocKMax;
@@ -982,6 +978,18 @@ __global__ void noalloc_prepare_kernel(ScanState* st, uint32_t* err) {
   }
 }
 
+// Bound on each device-side wait: 2 s, or FPS_NOALLOC_TIMEOUT_NS when that is set to a
+// positive integer (read on every call, so a test can make one call's waits run out).
+uint64_t noalloc_timeout_ns() {
+  const char* v = std::getenv("FPS_NOALLOC_TIMEOUT_NS");
+  if (v && *v) {
+    char* end = nullptr;
+    const unsigned long long t = std::strtoull(v, &end, 10);
+    if (end && *end == '\0' && t > 0) return t;
+  }
+  return 2000000000ull;
+}
+
 // A device-side failure (a bounded wait that ran out) is reported to the caller
 // as *out_count = -1, since the error word itself is not the caller's memory.
 __global__ void noalloc_finish_kernel(const uint32_t* err, int32_t* out_count) {
@@ -1009,7 +1017,11 @@ extern "C" fps_status fps_search_noalloc(fps_library lib, const uint64_t* query,
   if (noalloc_scratch(L->device, &base) != cudaSuccess) {
     status = FPS_ERR_CUDA;
   } else if (L->n == 0 || k == 0) {
-    if (cudaMemsetAsync(out_count, 0, sizeof(int32_t), s) != cudaSuccess) status = FPS_ERR_CUDA;
+    // count 0; with no records every slot up to k holds -1 (all bytes 0xFF), as on every path
+    if (cudaMemsetAsync(out_count, 0, sizeof(int32_t), s) != cudaSuccess ||
+        (k > 0 && (cudaMemsetAsync(out_index, 0xFF, sizeof(int32_t) * k, s) != cudaSuccess ||
+                   cudaMemsetAsync(out_dist, 0xFF, sizeof(int32_t) * k, s) != cudaSuccess)))
+      status = FPS_ERR_CUDA;
   } else {
     ScanState* st = reinterpret_cast<ScanState*>(base);
     uint32_t* err = reinterpret_cast<uint32_t*>(base + kNoAllocStateBytes);
@@ -1017,7 +1029,7 @@ extern "C" fps_status fps_search_noalloc(fps_library lib, const uint64_t* query,
     noalloc_prepare_kernel<<<1, 192, 0, s>>>(st, err);
     if (cudaGetLastError() != cudaSuccess ||
         launch_cfg<kSmallWarps, kSmallCap>(L->dev, query, k, st, cand, out_index, out_dist, out_count, err,
-                                           L->num_sms, 2000000000ull, false, s) != cudaSuccess) {
+                                           L->num_sms, noalloc_timeout_ns(), false, s) != cudaSuccess) {
       status = FPS_ERR_CUDA;
     } else {
       noalloc_finish_kernel<<<1, 32, 0, s>>>(err, out_count);

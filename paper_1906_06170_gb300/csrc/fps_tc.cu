@@ -145,8 +145,8 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
 }
 
 // Instruction descriptor of kind::f8f6f4: dense, A = B = E4M3 (format 0),
-// D = F32 (format 1), both K-major, N = 256 (N >> 3 at bit 17), M = 128
-// (M >> 4 at bit 24).
+// D = F16 (format 0 at bits 4-5; every sum is an integer <= 166, exact in FP16),
+// both K-major, N = 256 (N >> 3 at bit 17), M = 128 (M >> 4 at bit 24).
 __device__ __forceinline__ uint32_t instr_desc() {
   uint32_t d = 0;
   d |= 0u << 4;                           // D format: F16
@@ -833,13 +833,9 @@ __global__ void __launch_bounds__(kThreads, 1)
 cudaError_t launch_tc(const DevLib& lib, const BatchDev& b, const uint8_t* lib_op, const uint8_t* q_op, int64_t n_tc,
                       int n_qt, int num_sms, double timeout_s, cudaStream_t s) {
   const size_t smem = sizeof(TcSmem) + 1024;
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(tc_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  static std::atomic<uint64_t> configured{0};
+  cudaError_t e = smem_attr_once(tc_scan_kernel, smem, &configured);
+  if (e != cudaSuccess) return e;
   const uint64_t tns = static_cast<uint64_t>((timeout_s > 0 ? timeout_s : 2.0) * 1e9);
   tc_scan_kernel<<<num_sms, kThreads, smem, s>>>(lib, b, lib_op, q_op, n_tc, n_qt, tns);
   return cudaGetLastError();

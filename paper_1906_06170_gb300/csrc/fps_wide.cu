@@ -401,12 +401,9 @@ cudaError_t launch_wide(const WideLib& L, const uint64_t* q, int k, WideState* s
                         cudaStream_t s) {
   auto kern = wide_scan_kernel<METRIC, WARPS, CAP>;
   const size_t smem = sizeof(unsigned long long) * merge_cap(WARPS, CAP);
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  static std::atomic<uint64_t> configured{0};   // one per instantiation
+  cudaError_t e = smem_attr_once(kern, smem, &configured);
+  if (e != cudaSuccess) return e;
   if (num_sms > kMaxBlocks) return cudaErrorInvalidConfiguration;
   kern<<<num_sms, WARPS * 32, smem, s>>>(L, q, k, st, cand, bcnt, oi, on, od, oc);
   return cudaGetLastError();

@@ -41,3 +41,37 @@ def test_device_wait_timeout_is_reported_and_recovered(gpu_lib):
         assert np.array_equal(oi.cpu().numpy(), before_i) and np.array_equal(od.cpu().numpy(), before_d)
     finally:
         fps.fps_release(lib)
+
+
+def test_tensor_core_wait_timeout_is_reported_and_recovered(gpu_lib):
+    """The tensor-core batch: with a 1 ns bound every pipeline wait (copy landed, stage free,
+    accumulator full or free, hand-off ring room) gives up at its first miss.  Each warp then
+    stops issuing; the copy producer waits (at least 1 s) for its bulk copies in flight and the
+    MMA thread for its MMAs before the CTA frees its TMEM.  The call reports FPS_ERR_TIMEOUT in
+    both forms, and the same library and stream return the same results afterwards."""
+    fps = gpu_lib
+    n, Q = 5_000_000, 512
+    lib = fps.fps_library_load(packed=synth.packed(n, 31), flags=fps.FPS_LOAD_TC_OPERAND)
+    try:
+        qs = synth.packed(Q, 1031)
+        ks = synth.k_mix(Q, seed=31)
+        bi, bd, bc, _ = fps.fps_search_batch(lib, qs, ks, path=fps.FPS_PATH_TC_FP8, flat=True)
+        assert np.array_equal(bc, np.minimum(ks, n))
+        with pytest.raises(fps.FpsError) as e:
+            fps.fps_search_batch(lib, qs, ks, path=fps.FPS_PATH_TC_FP8, timeout_s=1e-9)
+        assert e.value.status == fps.FPS_ERR_TIMEOUT
+        qd = torch.from_numpy(qs.view(np.int64).copy()).cuda()
+        with pytest.raises(fps.FpsError) as e:
+            fps.fps_search_batch(lib, qd, ks, path=fps.FPS_PATH_TC_FP8, timeout_s=1e-9)
+            fps.fps_sync(lib)
+        assert e.value.status == fps.FPS_ERR_TIMEOUT
+        for _ in range(2):
+            ai, ad, ac, _ = fps.fps_search_batch(lib, qs, ks, path=fps.FPS_PATH_TC_FP8, flat=True)
+            assert np.array_equal(ac, bc) and np.array_equal(ai, bi) and np.array_equal(ad, bd)
+        oi, od, oc, off = fps.fps_search_batch(lib, qd, ks, path=fps.FPS_PATH_TC_FP8)
+        fps.fps_sync(lib)
+        assert np.array_equal(oc.cpu().numpy(), bc)
+        assert np.array_equal(oi.cpu().numpy()[: off[-1]], bi[: off[-1]])
+        assert np.array_equal(od.cpu().numpy()[: off[-1]], bd[: off[-1]])
+    finally:
+        fps.fps_release(lib)

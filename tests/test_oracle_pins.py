@@ -176,7 +176,7 @@ def test_parse_formats_and_errors():
 
 
 def test_combined_and_sorted_shards():
-    # The text after Fig. 3: strides searched separately, results combined and sorted.
+    # The text after Fig. 3: strides searched separately, their lists merged and re-sorted.
     n = 3000
     rows = synth.packed_to_strings(synth.packed(n, 0))
     q = synth.packed_to_strings(synth.packed(1, 1001))[0]

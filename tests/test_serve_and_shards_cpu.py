@@ -1,5 +1,5 @@
 """Host logic without a GPU: the serving loop's scheduling (fake back end), the
-shard merge against the oracle's "combined and sorted", and the multi-rank
+shard merge against the oracle's merge of the strides' lists, and the multi-rank
 shard path over torch.distributed gloo (world size 2)."""
 import os
 import socket

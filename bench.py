@@ -49,6 +49,8 @@ def parse_args():
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--n", type=int, default=PAPER_N, help="library records")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--headline-only", action="store_true",
+                   help="default workload: skip the other workloads' entries (1M latency, batched, learned)")
     p.add_argument("--workload", default="single",
                    choices=["single", "batch", "learned", "serve", "latency", "shards", "wide", "cluster"],
                    help="single: 16 sequential single queries per step (default); "
@@ -126,14 +128,19 @@ POPC32_PER_COMPARISON = 6.0
 SMS, SM_MAX_MHZ = 152, 2070.0
 
 
-def measured_peak_tflops_fp8():
-    """FP8 dense peak taken as 2 x the measured BF16 burst (the nominal FP8/BF16 ratio)."""
+# dense tensor rates relative to BF16 (nominal: FP8 4.5 and FP4 13.5 against BF16 2.25 PFLOP/s)
+TENSOR_RATIO = {"fp8": 2.0, "fp4": 6.0}
+
+
+def measured_peak_tflops(fmt: str = "fp8"):
+    """Dense peak of an FP8 or FP4 contraction: the measured BF16 burst x the nominal ratio."""
+    r = TENSOR_RATIO[fmt]
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
         with open(path) as f:
-            return 2.0 * float(json.load(f)["bf16_tflops"]), "2 x measured bf16 burst (MEASURED_PEAKS.json)"
+            return r * float(json.load(f)["bf16_tflops"]), f"{r:g} x measured bf16 burst (MEASURED_PEAKS.json)"
     except (OSError, KeyError, ValueError):
-        return 2.0 * 1900.0, "2 x fallback 1.9 PFLOP/s bf16"
+        return r * 1900.0, f"{r:g} x fallback 1.9 PFLOP/s bf16"
 
 
 def measured_peak_gbs():
@@ -145,6 +152,14 @@ def measured_peak_gbs():
         return 6800.0, "fallback"
 
 
+def scan_kernel_source_hash() -> str:
+    """Hash of the single-query scan's device code: fps_scan.cu up to its host-side launch code
+    (host-only edits further down leave the profiled kernel unchanged)."""
+    text = open(SCAN_SRC, "rb").read()
+    cut = text.find(b"cudaError_t configure_cfg()")
+    return hashlib.sha256(text[:cut if cut > 0 else len(text)]).hexdigest()[:16]
+
+
 def profile_traffic():
     """Per-launch DRAM bytes of the scan kernel from the committed ncu summary, if it
     was taken on the current kernel source (matching hash); else None."""
@@ -152,10 +167,10 @@ def profile_traffic():
         text = open(PROFILE).read()
     except OSError:
         return None
-    src_hash = hashlib.sha256(open(SCAN_SRC, "rb").read()).hexdigest()[:16]
+    src_hash = scan_kernel_source_hash()
     traffic, h = None, None
     for line in text.splitlines():
-        if line.startswith("source_sha256_16:"):
+        if line.startswith("kernel_source_sha256_16:"):
             h = line.split(":", 1)[1].strip()
         if line.startswith("dram_bytes_per_launch:"):
             traffic = float(line.split(":", 1)[1].strip())
@@ -243,6 +258,7 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": value / PAPER_GCPS, "dtype": "u8",
             "data": "synthetic",
             "config": workload_config(args.n, ws),
+            "sampled_records_per_step": records,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": f"each step: 1 query (seed 1001) x the first {records:,} of the "
                                        f"{args.n:,} records, parse + distances on {threads} threads + full sort"},
@@ -265,8 +281,10 @@ def run_gb300(args):
     dev = torch.device("cuda", local)
 
     n = args.n
+    legs = ws == 1 and not args.headline_only
     packed = synth.packed(n, 0)
-    lib = fps.fps_library_load(packed=packed, device=local)
+    # the batched legs need the tensor-core operand; the headline scan never reads it
+    lib = fps.fps_library_load(packed=packed, device=local, flags=fps.FPS_LOAD_TC_OPERAND if legs else 0)
     info = fps.fps_library_info_get(lib)
     del packed
     qs = synth.packed(QUERIES_PER_STEP * ws, 1001)[rank * QUERIES_PER_STEP:(rank + 1) * QUERIES_PER_STEP]
@@ -361,13 +379,15 @@ def run_gb300(args):
                 "vs_baseline_note": "paper: 95,417,114 molecules in ~40 min on an i5-6500 (Sec. 2.2); "
                                     "other hardware, PubChem data -- context only",
                 "dtype": "u64", "data": "synthetic",
-                "config": {**workload_config(n, ws),
-                           "l2": f"library {info['n_tiles'] * 3072 / 1e9:.2f} GB >> 129 MB L2: every "
-                                 "step streams from HBM, no flush needed"},
+                "config": workload_config(n, ws),
+                "l2": f"library {info['n_tiles'] * 3072 / 1e9:.2f} GB >> 129 MB L2: every step streams from "
+                      "HBM, no flush needed",
                 "roofline": roof, "clocks": clk,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": QUERIES_PER_STEP * 24,
                         "d2h_bytes_per_step": QUERIES_PER_STEP * (4 + 8 * K) + 4},
                 "gpu_launches": args.steps * QUERIES_PER_STEP}
+        if legs:
+            line["workloads"] = other_workloads(lib, n, args)
         if not args.no_cpu_baseline and ws == 1:
             line["cpu_baseline"] = cpu_oracle_throughput(4_000_000, 8, "")
         print(json.dumps(line), flush=True)
@@ -376,7 +396,7 @@ def run_gb300(args):
         dist.destroy_process_group()
 
 
-def run_latency(args):
+def latency_entry(n: int, steps: int, warmup: int) -> dict:
     """Single query over a 1,000,000-record library (24 MB, inside the 129 MB L2): warm latency (library
     cached in L2 by the previous query), cold latency (a 512 MB scratch buffer written before each query
     evicts it), and end-to-end latency through the C ABI with host buffers.  Device latencies are taken
@@ -388,7 +408,6 @@ def run_latency(args):
     import synth
 
     torch.cuda.set_device(0)
-    n = args.n if args.n != PAPER_N else 1_000_000
     lib = fps.fps_library_load(packed=synth.packed(n, 0))
     info = fps.fps_library_info_get(lib)
     q = synth.packed(1, synth.query_seed(0))
@@ -418,12 +437,12 @@ def run_latency(args):
             ts.append(a.elapsed_time(b) * 1e3)
         return np.array(ts)
 
-    for _ in range(max(args.warmup, 3)):
+    for _ in range(max(warmup, 3)):
         one()
     torch.cuda.synchronize()
     clocks = ClockSampler(0)
     clocks.start()
-    reps = max(args.steps, 20)
+    reps = max(steps, 20)
     warm = timed(False, reps)
     cold = timed(True, max(reps // 4, 10))
     call = timed(False, max(reps // 4, 10), busy=False)
@@ -436,6 +455,7 @@ def run_latency(args):
         e2e.append((time.perf_counter() - t0) * 1e6)
     e2e = np.array(e2e)
     assert len(res_i) == min(K, n) and np.all(np.diff(res_d) >= 0), "latency results malformed"
+    del scratch
     # algorithmic bytes of the bucketed scan (records in buckets within the k-th distance of the query)
     bc = info["bucket_count"]
     pq = int(np.unpackbits(q.view(np.uint8), bitorder="little")[:166].sum())
@@ -443,46 +463,77 @@ def run_latency(args):
     alg = 24.0 * bc[max(0, pq - tk): min(166, pq + tk) + 1].sum() + 8.0 * K
     peak, peak_kind = measured_peak_gbs()
     p50w, p50c = float(np.median(warm)), float(np.median(cold))
-    line = {"metric": METRIC, "value": n / (p50w * 1e-6) / 1e9, "unit": UNIT, "n_gpus": 1, "steps": reps,
-            "warmup": max(args.warmup, 3), "ms_per_step": p50w / 1e3, "higher_is_better": True,
+    fps.fps_release(lib)
+    return {"metric": METRIC, "value": n / (p50w * 1e-6) / 1e9, "unit": UNIT, "n_gpus": 1, "steps": reps,
+            "warmup": max(warmup, 3), "ms_per_step": p50w / 1e3, "higher_is_better": True,
             "dtype": "u64", "data": "synthetic",
             "latency_us": {"warm_p50": p50w, "warm_p99": float(np.percentile(warm, 99)),
                            "cold_p50": p50c, "cold_p99": float(np.percentile(cold, 99)),
                            "call_p50": float(np.median(call)),
-                       "e2e_host_p50": float(np.median(e2e)), "e2e_host_p99": float(np.percentile(e2e, 99))},
+                           "e2e_host_p50": float(np.median(e2e)), "e2e_host_p99": float(np.percentile(e2e, 99))},
             "latency_note": "warm/cold: device time of the search (events on the launching stream, GPU busy "
                             "while the host enqueues it); call: the same with the GPU idle until the launch "
                             "arrives (adds the host's launch time); e2e_host: host buffers through the C ABI, "
                             "wall clock",
             "cold_value": n / (p50c * 1e-6) / 1e9,
-            "roofline_cold": {"bound": "hbm", "achieved": alg / (p50c * 1e-6) / 1e9, "peak": peak, "unit": "GB/s",
-                              "frac": alg / (p50c * 1e-6) / 1e9 / peak, "algorithmic_bytes_per_launch": alg,
-                              "note": "a 24 MB launch is dominated by its fixed start and merge time"},
+            "roofline": {"bound": "hbm", "achieved": alg / (p50c * 1e-6) / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": alg / (p50c * 1e-6) / 1e9 / peak, "algorithmic_bytes_per_launch": alg,
+                         "traffic": None, "kernel": "scan_single_kernel<16,256>", "basis": "cold p50",
+                         "note": "a 24 MB launch is dominated by its fixed start and merge time"},
             "config": {"workload": f"{n:,} generated records (seed 0, 1% planted near-duplicates), 1 query "
                                    f"(seed 1000), k={K}; warm = library in L2 from the previous query, cold = "
                                    f"512 MB written before each query", "n_records": n, "k": K,
                        "peak_source": peak_kind},
             "clocks": clk,
             "e2e": {"value": n / (float(np.median(e2e)) * 1e-6) / 1e9, "unit": UNIT, "h2d_bytes_per_step": 32,
-                    "d2h_bytes_per_step": 8 + 8 * K},
+                    "d2h_bytes_per_step": 8 + 8 * K, "basis": "p50 wall clock per call"},
             "gpu_launches": 1}
-    print(json.dumps(line), flush=True)
-    fps.fps_release(lib)
 
 
-def run_batch(args):
-    """Batched workload: Q queries with k drawn from {1, 10, 30, 100, 1000} in one call per step."""
+def other_workloads(lib, n: int, args) -> dict:
+    """The other configurations, each timed on its own (CUDA events, clocks sampled per leg), on the
+    resident library of the headline: 1M-record single-query latency, the 4096-query mixed-k batch on
+    the FP8 tensor cores and on the popcount batch kernel, and the learned bound with its comparisons."""
+    leg = max(3, min(args.steps, 10))
+    warm = max(3, min(args.warmup, 3))
+    out = {}
+    t0 = time.perf_counter()
+    out["latency_1M"] = latency_entry(1_000_000, max(args.steps, 20), warm)
+    out["tc_fp8"] = batch_entry(lib, n, 4096, "tc_fp8", leg, warm)
+    out["popc_batch"] = batch_entry(lib, n, 4096, "popc_batch", max(2, min(args.steps // 5, 4)), warm, e2e_steps=2)
+    out["learned"] = learned_entry(lib, n, 4096, leg, warm)
+    out["wall_s"] = round(time.perf_counter() - t0, 1)
+    return out
+
+
+def run_latency(args):
+    n = args.n if args.n != PAPER_N else 1_000_000
+    print(json.dumps(latency_entry(n, args.steps, args.warmup)), flush=True)
+
+
+def tc_roofline(ms: float, Q: int, n: int, n_tiles: int, kernel: str, fmt: str) -> dict:
+    """Tensor roofline of a batched tensor-core call: the MMA work over the padded operand tiles
+    (K = 192, records padded per popcount bucket) and the method's own work (2 x 166 x Q x N)."""
+    flop = 2.0 * 192 * Q * n_tiles * 128
+    useful = 2.0 * 166 * Q * n
+    peak, basis = measured_peak_tflops(fmt)
+    ach = flop / (ms / 1e3) / 1e12
+    return {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+            "frac_method_flop": useful / (ms / 1e3) / 1e12 / peak, "traffic": None, "kernel": kernel,
+            "flop_per_call": flop, "method_flop_per_call": useful,
+            "basis": "whole batched call (bounds, query operand, scan, select) timed with CUDA events",
+            "peak_source": basis}
+
+
+def batch_entry(lib, n: int, Q: int, path_name: str, steps: int, warmup: int, e2e_steps: int = 3) -> dict:
+    """Q queries (seed 1002) with k drawn from {1, 10, 30, 100, 1000}, one batched call per step on a
+    resident library; end to end through a captured batch plan with host buffers."""
     import torch
 
     import paper_1906_06170_gb300 as fps
     import synth
 
-    paths = {"popc_batch": fps.FPS_PATH_POPC_BATCH, "popc": fps.FPS_PATH_POPC, "tc_fp8": fps.FPS_PATH_TC_FP8,
-             "tc_i8": fps.FPS_PATH_TC_I8, "learned": fps.FPS_PATH_LEARNED}
-    torch.cuda.set_device(0)
-    n, Q = args.n, args.queries
-    flags = fps.FPS_LOAD_TC_OPERAND if args.path in ("tc_fp8", "tc_i8") else 0
-    lib = fps.fps_library_load(packed=synth.packed(n, 0), flags=flags)
+    path = batch_path_code(fps, path_name)
     qs = synth.packed(Q, synth.query_seed(2))
     ks = synth.k_mix(Q, seed=2)
     qd = torch.from_numpy(qs.view(np.int64).copy()).cuda()
@@ -494,10 +545,10 @@ def run_batch(args):
     stats = fps.fps_search_stats()
 
     def step():
-        fps.fps_search_batch(lib, qd, ks, path=paths[args.path], out_index=oi, out_dist=od, out_count=oc,
+        fps.fps_search_batch(lib, qd, ks, path=path, out_index=oi, out_dist=od, out_count=oc,
                              offsets=off, stream=stream, stats=stats)
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
     torch.cuda.synchronize()
     clocks = ClockSampler(0)
@@ -505,81 +556,90 @@ def run_batch(args):
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         step()
     t1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
-    ms = t0.elapsed_time(t1) / args.steps
+    ms = t0.elapsed_time(t1) / steps
     cnt = oc.cpu().numpy()
     assert np.all(cnt == np.minimum(ks, n)), "batch results malformed"
     value = Q * n / (ms / 1e3) / 1e9
     info = fps.fps_library_info_get(lib)
-    if args.path.startswith("tc"):
-        # the contraction over 256-record tensor tiles (records padded per popcount bucket), per call
-        flop = 2.0 * 192 * Q * ((info["n_tiles"] + 1) // 2) * 256
-        peak, basis = measured_peak_tflops_fp8()
-        ach = flop / (ms / 1e3) / 1e12
-        roof = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                "traffic": None, "kernel": "tc_scan_kernel", "flop_per_call": flop,
-                "basis": "whole batched call (bounds, query operand, scan, select) timed with CUDA events",
-                "peak_source": basis}
+    if path_name.startswith("tc"):
+        fmt = path_name.split("_")[1]
+        roof = tc_roofline(ms, Q, n, 2 * ((info["n_tiles"] + 1) // 2) if fmt == "fp8" else info["n_tiles"],
+                           f"tc_scan_kernel ({fmt})", fmt)
     else:
         peak = POPC32_PER_SM_CLK / POPC32_PER_COMPARISON * SMS * SM_MAX_MHZ * 1e6 / 1e9
         roof = {"bound": "alu", "achieved": value, "peak": peak, "unit": "G-comparisons/s", "frac": value / peak,
                 "traffic": None, "kernel": "batch_popc_kernel",
                 "peak_source": "POPC32 16 per SM per clock (measured) x 152 SMs x 2070 MHz / 6 per comparison"}
     # end to end through a captured batch plan (CUDA graph): host queries in, host results out
-    e2e = None
-    if args.path in ("tc_fp8", "popc_batch"):
-        plan = fps.fps_batch_plan_create(lib, ks, path=paths[args.path])
-        for _ in range(2):
-            fps.fps_batch_plan_run(plan, qs, flat=True)
-        t_e = time.perf_counter()
-        e2e_steps = max(2, min(args.steps, 5))
-        for _ in range(e2e_steps):
-            ri, rd, rc, ro = fps.fps_batch_plan_run(plan, qs, flat=True)
-        e2e_s = (time.perf_counter() - t_e) / e2e_steps
-        assert np.array_equal(rc, np.minimum(ks, n)), "plan results malformed"
-        fps.fps_batch_plan_release(plan)
-        e2e = {"value": Q * n / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": Q * 24,
-               "d2h_bytes_per_step": int(np.sum(ks)) * 8 + Q * 4, "ms_per_step": e2e_s * 1e3,
-               "via": "fps_batch_plan_run (captured graph, host buffers)"}
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "queries_per_s": Q / (ms / 1e3), "dtype": "u64" if args.path.startswith("popc") else args.path,
-            "data": "synthetic", "fallbacks": int(stats.fallbacks),
+    plan = fps.fps_batch_plan_create(lib, ks, path=path)
+    fps.fps_batch_plan_run(plan, qs, flat=True)
+    t_e = time.perf_counter()
+    for _ in range(e2e_steps):
+        ri, rd, rc, ro = fps.fps_batch_plan_run(plan, qs, flat=True)
+    e2e_s = (time.perf_counter() - t_e) / e2e_steps
+    assert np.array_equal(rc, np.minimum(ks, n)), "plan results malformed"
+    fps.fps_batch_plan_release(plan)
+    e2e = {"value": Q * n / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": Q * 24,
+           "d2h_bytes_per_step": int(np.sum(ks)) * 8 + Q * 4, "ms_per_step": e2e_s * 1e3, "steps": e2e_steps,
+           "via": "fps_batch_plan_run (captured graph, host buffers)"}
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": steps,
+            "warmup": warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "queries_per_s": Q / (ms / 1e3), "dtype": "u64" if path_name.startswith("popc") else path_name,
+            "data": "synthetic", "fallbacks": int(stats.fallbacks), "candidates": int(stats.candidates),
             "config": {"workload": f"{n:,} generated records (seed 0), {Q} queries (seed 1002) with k from "
-                                   f"{{1,10,30,100,1000}} per batched call, path {args.path}",
+                                   f"{{1,10,30,100,1000}} per batched call, path {path_name}",
                        "n_records": n, "queries": Q},
-            "clocks": clk, "roofline": roof,
-            "gpu_launches": args.steps * (4 if args.path.startswith("tc") else 3)}
-    if e2e is not None:
-        line["e2e"] = e2e
+            "clocks": clk, "roofline": roof, "e2e": e2e,
+            "gpu_launches": steps * (4 if path_name.startswith("tc") else 3)}
+
+
+def batch_path_code(fps, name: str) -> int:
+    return {"popc_batch": fps.FPS_PATH_POPC_BATCH, "popc": fps.FPS_PATH_POPC, "tc_fp8": fps.FPS_PATH_TC_FP8,
+            "tc_i8": fps.FPS_PATH_TC_I8, "learned": fps.FPS_PATH_LEARNED}[name]
+
+
+def run_batch(args):
+    """Batched workload: Q queries with k drawn from {1, 10, 30, 100, 1000} in one call per step."""
+    import torch
+
+    import paper_1906_06170_gb300 as fps
+    import synth
+
+    torch.cuda.set_device(0)
+    flags = fps.FPS_LOAD_TC_OPERAND if args.path in ("tc_fp8", "tc_i8") else 0
+    lib = fps.fps_library_load(packed=synth.packed(args.n, 0), flags=flags)
+    line = batch_entry(lib, args.n, args.queries, args.path, args.steps, args.warmup,
+                       e2e_steps=max(2, min(args.steps, 5)))
     print(json.dumps(line), flush=True)
     fps.fps_release(lib)
 
 
-def run_learned(args):
-    """Learned threshold: train on exact T_30 of 4 x 10M-record libraries, search the full library."""
+def learned_entry(lib, n: int, Q: int, steps: int, warmup: int) -> dict:
+    """Learned threshold: an MLP trained on the exact 30th distances of 4 x 10M-record libraries predicts
+    each query's bound on the resident library; beside it the same batch with the sampled bound (no
+    prediction) and with a per-popcount quantile table (a non-learned predictor)."""
     import torch
 
     import paper_1906_06170_gb300 as fps
     import synth
     from paper_1906_06170_gb300 import learn
 
-    torch.cuda.set_device(0)
-    k, Q = 30, args.queries
+    k = 30
     n_train_lib = int(os.environ.get("FPS_LEARN_TRAIN_N", 10_000_000))
     per_lib = int(os.environ.get("FPS_LEARN_PER_LIB", 500_000))
     t_prep = time.perf_counter()
     qs_all, ts_all = [], []
     for seed in (1, 2, 3, 4):
-        lib = fps.fps_library_load(packed=synth.packed(n_train_lib, seed), flags=fps.FPS_LOAD_TC_OPERAND)
+        tl = fps.fps_library_load(packed=synth.packed(n_train_lib, seed), flags=fps.FPS_LOAD_TC_OPERAND)
         q = torch.from_numpy(synth.packed(per_lib, 100 + seed).view(np.int64).copy()).cuda()
-        ts_all.append(learn.exact_kth(lib, q, k))
+        ts_all.append(learn.exact_kth(tl, q, k))
         qs_all.append(q)
-        fps.fps_release(lib)
+        fps.fps_release(tl)
     qtr, ttr = torch.cat(qs_all), torch.cat(ts_all)
     t_labels = time.perf_counter() - t_prep
     model = fps.fps_mlp_create(0)
@@ -593,8 +653,6 @@ def run_learned(args):
     table = learn.popc_quantile_table(qtr, ttr, 0.9)
     del qtr, ttr
 
-    n = args.n
-    lib = fps.fps_library_load(packed=synth.packed(n, 0), flags=fps.FPS_LOAD_TC_OPERAND)
     qcal = torch.from_numpy(synth.packed(4096, 999).view(np.int64).copy()).cuda()
     tcal = learn.exact_kth(lib, qcal, k)
     offset = learn.calibrate_offset(model, qcal, tcal, max_fallback=0.0025)
@@ -608,17 +666,17 @@ def run_learned(args):
     oc = torch.empty(Q, dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
 
-    def timed(fn, steps, warmup):
-        for _ in range(warmup):
+    def timed(fn, nsteps, nwarm):
+        for _ in range(nwarm):
             fn()
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        for _ in range(steps):
+        for _ in range(nsteps):
             fn()
         b.record(stream)
         torch.cuda.synchronize()
-        return a.elapsed_time(b) / steps
+        return a.elapsed_time(b) / nsteps
 
     st_l = fps.fps_search_stats()
 
@@ -629,16 +687,20 @@ def run_learned(args):
 
     clocks = ClockSampler(0)
     clocks.start()
-    ms_l = timed(learned_step, args.steps, args.warmup)
+    ms_l = timed(learned_step, steps, warmup)
     clk = clocks.stop()
     res_l = (oi.clone(), od.clone())
+    assert np.all(oc.cpu().numpy() == min(k, n)), "learned results malformed"
     st_p = fps.fps_search_stats()
 
     def pilot_step():
         fps.fps_search_batch(lib, qd, ks, path=fps.FPS_PATH_TC_FP8, out_index=oi, out_dist=od, out_count=oc,
                              offsets=off, stream=stream, stats=st_p)
 
-    ms_p = timed(pilot_step, max(2, args.steps // 2), 1)
+    clocks = ClockSampler(0)
+    clocks.start()
+    ms_p = timed(pilot_step, steps, 1)
+    clk_p = clocks.stop()
     assert torch.equal(res_l[0], oi) and torch.equal(res_l[1], od), "learned and sampled-bound results differ"
     st_t = fps.fps_search_stats()
     tau_t = torch.from_numpy(learn.table_tau(table, qs, t_offset)).cuda()
@@ -647,17 +709,48 @@ def run_learned(args):
         fps.fps_search_batch(lib, qd, ks, path=fps.FPS_PATH_LEARNED, tau=tau_t, out_index=oi, out_dist=od,
                              out_count=oc, offsets=off, stream=stream, stats=st_t)
 
-    ms_t = timed(table_step, max(2, args.steps // 2), 1)
+    ms_t = timed(table_step, max(2, steps // 2), 1)
     assert torch.equal(res_l[0], oi) and torch.equal(res_l[1], od), "learned and table-bound results differ"
+    # end to end through the public API: pinned host queries in, prediction, search, results to pinned host
+    qh = torch.from_numpy(qs.view(np.int64).copy()).pin_memory()
+    ri = torch.empty(int(off[-1]), dtype=torch.int32).pin_memory()
+    rd = torch.empty_like(ri).pin_memory()
+    rc = torch.empty(Q, dtype=torch.int32).pin_memory()
+
+    def e2e_step():
+        qdev = qh.to("cuda", non_blocking=True)
+        tau = learn.predict_tau(model, qdev, offset).contiguous()
+        fps.fps_search_batch(lib, qdev, ks, path=fps.FPS_PATH_LEARNED, tau=tau, out_index=oi, out_dist=od,
+                             out_count=oc, offsets=off, stream=stream)
+        ri.copy_(oi, non_blocking=True)
+        rd.copy_(od, non_blocking=True)
+        rc.copy_(oc, non_blocking=True)
+        torch.cuda.synchronize()
+
+    e2e_step()
+    e2e_n = max(2, min(steps, 5))
+    t_e = time.perf_counter()
+    for _ in range(e2e_n):
+        e2e_step()
+    e2e_s = (time.perf_counter() - t_e) / e2e_n
+    assert torch.equal(ri, res_l[0].cpu()) and torch.equal(rd, res_l[1].cpu()), "learned e2e results differ"
+    fps.fps_mlp_release(model)
     value = Q * n / (ms_l / 1e3) / 1e9
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_l, "higher_is_better": True, "scaling": "weak",
+    info = fps.fps_library_info_get(lib)
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": steps,
+            "warmup": warmup, "ms_per_step": ms_l, "higher_is_better": True, "scaling": "weak",
             "queries_per_s": Q / (ms_l / 1e3), "dtype": "fp8+bf16", "data": "synthetic",
             "fallbacks": int(st_l.fallbacks), "fallback_rate": st_l.fallbacks / Q,
             "candidates_learned": int(st_l.candidates), "candidates_sampled_bound": int(st_p.candidates),
             "calibration_offset": offset, "train_loss_per_epoch": hist,
+            "roofline": tc_roofline(ms_l, Q, n, 2 * ((info["n_tiles"] + 1) // 2), "tc_scan_kernel (fp8)", "fp8"),
+            "e2e": {"value": Q * n / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": Q * 24,
+                    "d2h_bytes_per_step": int(np.sum(ks)) * 8 + Q * 4, "ms_per_step": e2e_s * 1e3,
+                    "steps": e2e_n, "via": "pinned host queries -> fps_mlp_predict -> fps_search_batch "
+                                           "(FPS_PATH_LEARNED) -> pinned host results, wall clock"},
             "sampled_bound_tc": {"ms_per_step": ms_p, "queries_per_s": Q / (ms_p / 1e3),
-                                 "value": Q * n / (ms_p / 1e3) / 1e9},
+                                 "value": Q * n / (ms_p / 1e3) / 1e9, "candidates": int(st_p.candidates),
+                                 "fallbacks": int(st_p.fallbacks), "clocks": clk_p},
             "popc_table_bound": {"ms_per_step": ms_t, "queries_per_s": Q / (ms_t / 1e3),
                                  "value": Q * n / (ms_t / 1e3) / 1e9, "candidates": int(st_t.candidates),
                                  "fallbacks": int(st_t.fallbacks), "fallback_rate": st_t.fallbacks / Q,
@@ -669,8 +762,17 @@ def run_learned(args):
                                    f"{n:,} records (seed 0), {Q} queries (seed 1003), k={k}",
                        "n_records": n, "queries": Q, "k": k},
             "clocks": clk}
-    print(json.dumps(line), flush=True)
-    fps.fps_mlp_release(model)
+
+
+def run_learned(args):
+    import torch
+
+    import paper_1906_06170_gb300 as fps
+    import synth
+
+    torch.cuda.set_device(0)
+    lib = fps.fps_library_load(packed=synth.packed(args.n, 0), flags=fps.FPS_LOAD_TC_OPERAND)
+    print(json.dumps(learned_entry(lib, args.n, args.queries, args.steps, args.warmup)), flush=True)
     fps.fps_release(lib)
 
 

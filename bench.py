@@ -49,6 +49,10 @@ def parse_args():
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--n", type=int, default=PAPER_N, help="library records")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--split", default="replicas", choices=["replicas", "library"],
+                   help="N > 1: replicas (every rank its own library copy and queries, weak scaling) or library "
+                        "(rank r holds records [rN/n, (r+1)N/n); the same 16 queries on every rank; per-rank lists "
+                        "gathered and merged on rank 0, strong scaling)")
     p.add_argument("--headline-only", action="store_true",
                    help="default workload: skip the other workloads' entries (1M latency, batched, learned)")
     p.add_argument("--workload", default="single",
@@ -56,7 +60,8 @@ def parse_args():
                    help="single: 16 sequential single queries per step (default); "
                         "batch: --queries queries with mixed k in one batched call per step")
     p.add_argument("--queries", type=int, default=4096)
-    p.add_argument("--path", default="popc_batch", choices=["popc_batch", "popc", "tc_fp8", "tc_i8", "learned"])
+    p.add_argument("--path", default="popc_batch",
+                   choices=["popc_batch", "popc", "tc_fp8", "tc_fp4", "tc_i8", "learned", "auto"])
     return p.parse_args()
 
 
@@ -284,7 +289,8 @@ def run_gb300(args):
     legs = ws == 1 and not args.headline_only
     packed = synth.packed(n, 0)
     # the batched legs need the tensor-core operand; the headline scan never reads it
-    lib = fps.fps_library_load(packed=packed, device=local, flags=fps.FPS_LOAD_TC_OPERAND if legs else 0)
+    lib = fps.fps_library_load(packed=packed, device=local,
+                               flags=fps.FPS_LOAD_TC_OPERAND | fps.FPS_LOAD_TC_FP4 if legs else 0)
     info = fps.fps_library_info_get(lib)
     del packed
     qs = synth.packed(QUERIES_PER_STEP * ws, 1001)[rank * QUERIES_PER_STEP:(rank + 1) * QUERIES_PER_STEP]
@@ -396,6 +402,92 @@ def run_gb300(args):
         dist.destroy_process_group()
 
 
+def run_split(args):
+    """The library split across ranks (the paper's strides, Sec. 2.1): rank r searches records
+    [r N / n, (r + 1) N / n) for the same 16 queries, the k keys per query of every rank are
+    all-gathered (one collective per step), and rank 0 merges them (fps_merge_topk).  value =
+    16 x N / step time: the whole library per query, so the scaling is strong."""
+    import torch
+    import torch.distributed as dist
+
+    import paper_1906_06170_gb300 as fps
+    import synth
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n = args.n
+    lo, hi = rank * n // ws, (rank + 1) * n // ws
+    lib = fps.fps_library_load(packed=synth.packed(hi - lo, 0, start=lo), device=local)
+    qs = synth.packed(QUERIES_PER_STEP, 1001)
+    qd = torch.from_numpy(qs.view(np.int64).copy()).to(dev)
+    ks = np.full(QUERIES_PER_STEP, K, np.int32)
+    off = fps.batch_offsets(ks)
+    oi = torch.empty(QUERIES_PER_STEP * K, dtype=torch.int32, device=dev)
+    od = torch.empty_like(oi)
+    oc = torch.empty(QUERIES_PER_STEP, dtype=torch.int32, device=dev)
+    mine = torch.empty((2, QUERIES_PER_STEP * K), dtype=torch.int64, device=dev)
+    bufs = [torch.empty_like(mine) for _ in range(ws)]
+    stream = torch.cuda.current_stream()
+    merged = []
+
+    def step():
+        fps.fps_search_batch(lib, qd, ks, path=fps.FPS_PATH_POPC, out_index=oi, out_dist=od, out_count=oc,
+                             offsets=off, stream=stream)
+        mine[0].copy_(oi.to(torch.int64) + lo)
+        mine[1].copy_(od.to(torch.int64))
+        if ws > 1:
+            dist.all_gather(bufs, mine)
+        else:
+            bufs[0].copy_(mine)
+        if rank == 0:
+            h = [b.cpu().numpy() for b in bufs]
+            merged.clear()
+            for q in range(QUERIES_PER_STEP):
+                sl = slice(q * K, (q + 1) * K)
+                merged.append(fps.fps_merge_topk([(b[0, sl].astype(np.int32), b[1, sl].astype(np.int32))
+                                                  for b in h], K))
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    barrier()
+    dt = time.perf_counter() - t0
+    clk = clocks.stop()
+    fps.fps_sync(lib)
+    if ws > 1:
+        t = torch.tensor([dt], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dt = float(t.item())
+    if rank == 0:
+        assert all(len(i) == min(K, n) and np.all(np.diff(d) >= 0) for i, d in merged), "merged results malformed"
+        ms = dt / args.steps * 1e3
+        value = QUERIES_PER_STEP * n / (ms / 1e3) / 1e9
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "strong",
+                "vs_baseline": value / PAPER_GCPS, "dtype": "u64", "data": "synthetic",
+                "config": dict(workload_config(n, ws), parallelism=f"library split x{ws}"),
+                "timing": "wall clock per step including the all-gather and rank 0's merge, max over ranks",
+                "clocks": clk, "gpu_launches": args.steps * QUERIES_PER_STEP}
+        print(json.dumps(line), flush=True)
+    fps.fps_release(lib)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
 def latency_entry(n: int, steps: int, warmup: int) -> dict:
     """Single query over a 1,000,000-record library (24 MB, inside the 129 MB L2): warm latency (library
     cached in L2 by the previous query), cold latency (a 512 MB scratch buffer written before each query
@@ -500,6 +592,7 @@ def other_workloads(lib, n: int, args) -> dict:
     t0 = time.perf_counter()
     out["latency_1M"] = latency_entry(1_000_000, max(args.steps, 20), warm)
     out["tc_fp8"] = batch_entry(lib, n, 4096, "tc_fp8", leg, warm)
+    out["tc_fp4"] = batch_entry(lib, n, 4096, "tc_fp4", leg, warm)
     out["popc_batch"] = batch_entry(lib, n, 4096, "popc_batch", max(2, min(args.steps // 5, 4)), warm, e2e_steps=2)
     out["learned"] = learned_entry(lib, n, 4096, leg, warm)
     out["wall_s"] = round(time.perf_counter() - t0, 1)
@@ -511,10 +604,21 @@ def run_latency(args):
     print(json.dumps(latency_entry(n, args.steps, args.warmup)), flush=True)
 
 
-def tc_roofline(ms: float, Q: int, n: int, n_tiles: int, kernel: str, fmt: str) -> dict:
+TC_TILE_ROWS = {"fp8": 256, "fp4": 192}
+
+
+def tc_padded_records(n_tiles128: int, fmt: str) -> int:
+    """Records the contraction covers: the bucketed layout (128-record tiles, buckets padded to 256
+    records) rounded up to the format's library tiles."""
+    rows = TC_TILE_ROWS[fmt]
+    return (n_tiles128 * 128 + rows - 1) // rows * rows
+
+
+def tc_roofline(ms: float, Q: int, n: int, n_tiles128: int, kernel: str, fmt: str) -> dict:
     """Tensor roofline of a batched tensor-core call: the MMA work over the padded operand tiles
-    (K = 192, records padded per popcount bucket) and the method's own work (2 x 166 x Q x N)."""
-    flop = 2.0 * 192 * Q * n_tiles * 128
+    (K = 192, records padded per popcount bucket and to whole tiles) and the method's own work
+    (2 x 166 x Q x N)."""
+    flop = 2.0 * 192 * Q * tc_padded_records(n_tiles128, fmt)
     useful = 2.0 * 166 * Q * n
     peak, basis = measured_peak_tflops(fmt)
     ach = flop / (ms / 1e3) / 1e12
@@ -568,8 +672,7 @@ def batch_entry(lib, n: int, Q: int, path_name: str, steps: int, warmup: int, e2
     info = fps.fps_library_info_get(lib)
     if path_name.startswith("tc"):
         fmt = path_name.split("_")[1]
-        roof = tc_roofline(ms, Q, n, 2 * ((info["n_tiles"] + 1) // 2) if fmt == "fp8" else info["n_tiles"],
-                           f"tc_scan_kernel ({fmt})", fmt)
+        roof = tc_roofline(ms, Q, n, info["n_tiles"], f"tc_scan_kernel<{fmt}>", fmt)
     else:
         peak = POPC32_PER_SM_CLK / POPC32_PER_COMPARISON * SMS * SM_MAX_MHZ * 1e6 / 1e9
         roof = {"bound": "alu", "achieved": value, "peak": peak, "unit": "G-comparisons/s", "frac": value / peak,
@@ -591,6 +694,7 @@ def batch_entry(lib, n: int, Q: int, path_name: str, steps: int, warmup: int, e2
             "warmup": warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "queries_per_s": Q / (ms / 1e3), "dtype": "u64" if path_name.startswith("popc") else path_name,
             "data": "synthetic", "fallbacks": int(stats.fallbacks), "candidates": int(stats.candidates),
+            "tile_param": int(stats.tile_param),
             "config": {"workload": f"{n:,} generated records (seed 0), {Q} queries (seed 1002) with k from "
                                    f"{{1,10,30,100,1000}} per batched call, path {path_name}",
                        "n_records": n, "queries": Q},
@@ -598,9 +702,45 @@ def batch_entry(lib, n: int, Q: int, path_name: str, steps: int, warmup: int, e2
             "gpu_launches": steps * (4 if path_name.startswith("tc") else 3)}
 
 
+def mma_skip_fraction(qs: np.ndarray, tau: np.ndarray, bucket_count: np.ndarray, tile_rows: int = 256) -> dict:
+    """Share of the contraction's (128-query tile, library tile) products whose popcount-bucket lower
+    bound |popc q - popc x| exceeds the bound of every query in the tile, so that skipping them could
+    not change the result: for the queries in the batch's order and sorted by popcount."""
+    pq = np.unpackbits(qs.view(np.uint8), axis=1, bitorder="little")[:, :166].sum(1).astype(np.int64)
+    thr = np.clip(np.ceil(tau), 0, 166).astype(np.int64)
+    tiles = -(-np.asarray(bucket_count, np.int64) // tile_rows)        # library tiles per bucket
+    b = np.arange(167)
+
+    def frac(order):
+        skip = total = 0
+        for t0 in range(0, len(order), 128):
+            rows = order[t0:t0 + 128]
+            # bucket b is needed by the tile if some row has |pq - b| <= thr
+            need = (np.abs(pq[rows][:, None] - b[None, :]) <= thr[rows][:, None]).any(0)
+            skip += int(tiles[~need].sum())
+            total += int(tiles.sum())
+        return skip / max(total, 1)
+
+    return {"batch_order": frac(np.arange(len(pq))), "sorted_by_popcount": frac(np.argsort(pq, kind="stable"))}
+
+
+def learned_roofline(ms: float, Q: int, n: int, n_tiles128: int, path_used: int, value: float) -> dict:
+    """Roofline of the learned call by the kernel the autotuner ran it on."""
+    name = PATH_NAMES.get(path_used, "")
+    if name.startswith("tc_"):
+        return tc_roofline(ms, Q, n, n_tiles128, f"tc_scan_kernel<{name[3:]}>", name[3:])
+    peak = POPC32_PER_SM_CLK / POPC32_PER_COMPARISON * SMS * SM_MAX_MHZ * 1e6 / 1e9
+    return {"bound": "alu", "achieved": value, "peak": peak, "unit": "G-comparisons/s", "frac": value / peak,
+            "traffic": None, "kernel": "batch_popc_kernel or scan_single_kernel"}
+
+
 def batch_path_code(fps, name: str) -> int:
     return {"popc_batch": fps.FPS_PATH_POPC_BATCH, "popc": fps.FPS_PATH_POPC, "tc_fp8": fps.FPS_PATH_TC_FP8,
-            "tc_i8": fps.FPS_PATH_TC_I8, "learned": fps.FPS_PATH_LEARNED}[name]
+            "tc_fp4": fps.FPS_PATH_TC_FP4, "tc_i8": fps.FPS_PATH_TC_I8, "learned": fps.FPS_PATH_LEARNED,
+            "auto": fps.FPS_PATH_AUTO}[name]
+
+
+PATH_NAMES = {0: "auto", 1: "popc", 2: "popc_batch", 3: "tc_fp8", 4: "tc_i8", 5: "learned", 6: "tc_fp4"}
 
 
 def run_batch(args):
@@ -611,7 +751,8 @@ def run_batch(args):
     import synth
 
     torch.cuda.set_device(0)
-    flags = fps.FPS_LOAD_TC_OPERAND if args.path in ("tc_fp8", "tc_i8") else 0
+    flags = {"tc_fp8": fps.FPS_LOAD_TC_OPERAND, "tc_i8": fps.FPS_LOAD_TC_OPERAND, "tc_fp4": fps.FPS_LOAD_TC_FP4,
+             "auto": fps.FPS_LOAD_TC_OPERAND | fps.FPS_LOAD_TC_FP4}.get(args.path, 0)
     lib = fps.fps_library_load(packed=synth.packed(args.n, 0), flags=flags)
     line = batch_entry(lib, args.n, args.queries, args.path, args.steps, args.warmup,
                        e2e_steps=max(2, min(args.steps, 5)))
@@ -692,9 +833,12 @@ def learned_entry(lib, n: int, Q: int, steps: int, warmup: int) -> dict:
     res_l = (oi.clone(), od.clone())
     assert np.all(oc.cpu().numpy() == min(k, n)), "learned results malformed"
     st_p = fps.fps_search_stats()
+    # the same kernel without a prediction (the batch's sampled bounds)
+    pilot_path = int(st_l.path_used) if PATH_NAMES.get(int(st_l.path_used), "").startswith("tc_") \
+        else fps.FPS_PATH_TC_FP8
 
     def pilot_step():
-        fps.fps_search_batch(lib, qd, ks, path=fps.FPS_PATH_TC_FP8, out_index=oi, out_dist=od, out_count=oc,
+        fps.fps_search_batch(lib, qd, ks, path=pilot_path, out_index=oi, out_dist=od, out_count=oc,
                              offsets=off, stream=stream, stats=st_p)
 
     clocks = ClockSampler(0)
@@ -734,21 +878,25 @@ def learned_entry(lib, n: int, Q: int, steps: int, warmup: int) -> dict:
         e2e_step()
     e2e_s = (time.perf_counter() - t_e) / e2e_n
     assert torch.equal(ri, res_l[0].cpu()) and torch.equal(rd, res_l[1].cpu()), "learned e2e results differ"
+    info = fps.fps_library_info_get(lib)
+    skip = mma_skip_fraction(qs, learn.predict_tau(model, qd, offset).cpu().numpy(), info["bucket_count"])
     fps.fps_mlp_release(model)
     value = Q * n / (ms_l / 1e3) / 1e9
-    info = fps.fps_library_info_get(lib)
     return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": steps,
             "warmup": warmup, "ms_per_step": ms_l, "higher_is_better": True, "scaling": "weak",
             "queries_per_s": Q / (ms_l / 1e3), "dtype": "fp8+bf16", "data": "synthetic",
             "fallbacks": int(st_l.fallbacks), "fallback_rate": st_l.fallbacks / Q,
             "candidates_learned": int(st_l.candidates), "candidates_sampled_bound": int(st_p.candidates),
+            "mma_skip_fraction": skip,
             "calibration_offset": offset, "train_loss_per_epoch": hist,
-            "roofline": tc_roofline(ms_l, Q, n, 2 * ((info["n_tiles"] + 1) // 2), "tc_scan_kernel (fp8)", "fp8"),
+            "kernel_used": PATH_NAMES.get(int(st_l.path_used), str(int(st_l.path_used))),
+            "tile_param": int(st_l.tile_param),
+            "roofline": learned_roofline(ms_l, Q, n, info["n_tiles"], int(st_l.path_used), value),
             "e2e": {"value": Q * n / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": Q * 24,
                     "d2h_bytes_per_step": int(np.sum(ks)) * 8 + Q * 4, "ms_per_step": e2e_s * 1e3,
                     "steps": e2e_n, "via": "pinned host queries -> fps_mlp_predict -> fps_search_batch "
                                            "(FPS_PATH_LEARNED) -> pinned host results, wall clock"},
-            "sampled_bound_tc": {"ms_per_step": ms_p, "queries_per_s": Q / (ms_p / 1e3),
+            "sampled_bound_tc": {"kernel": PATH_NAMES.get(pilot_path), "ms_per_step": ms_p, "queries_per_s": Q / (ms_p / 1e3),
                                  "value": Q * n / (ms_p / 1e3) / 1e9, "candidates": int(st_p.candidates),
                                  "fallbacks": int(st_p.fallbacks), "clocks": clk_p},
             "popc_table_bound": {"ms_per_step": ms_t, "queries_per_s": Q / (ms_t / 1e3),
@@ -771,7 +919,7 @@ def run_learned(args):
     import synth
 
     torch.cuda.set_device(0)
-    lib = fps.fps_library_load(packed=synth.packed(args.n, 0), flags=fps.FPS_LOAD_TC_OPERAND)
+    lib = fps.fps_library_load(packed=synth.packed(args.n, 0), flags=fps.FPS_LOAD_TC_OPERAND | fps.FPS_LOAD_TC_FP4)
     print(json.dumps(learned_entry(lib, args.n, args.queries, args.steps, args.warmup)), flush=True)
     fps.fps_release(lib)
 
@@ -1084,6 +1232,8 @@ def main():
         run_learned(args)
     elif args.workload == "serve":
         run_serve(args)
+    elif args.split == "library":
+        run_split(args)
     else:
         run_gb300(args)
 

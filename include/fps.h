@@ -67,6 +67,8 @@ typedef struct fps_library_s* fps_library;
 #define FPS_LOAD_TC_OPERAND 0x4u  /* also build the 0/1 FP8 operand the tensor-core batch path needs
                                      (192 bytes per record, bucketed layout only) */
 #define FPS_LOAD_TC_INT8 0x8u     /* INT8 operand: always FPS_ERR_UNSUPPORTED (sm_103a has no tcgen05 kind::i8) */
+#define FPS_LOAD_TC_FP4 0x10u     /* also build the packed 0/1 FP4 operand of FPS_PATH_TC_FP4 (96 bytes per
+                                     record: two E2M1 keys per byte; bucketed layout only) */
 
 /*
  * Exactly one library source must be given: a file path, an in-memory text
@@ -119,6 +121,7 @@ typedef struct {
   int bucketed;                  /* 1 = popcount-bucketed layout (pruning on) */
   int has_tc_operand;            /* 1 = the FP8 tensor-core operand is resident */
   int64_t bucket_count[FPS_BITS + 1]; /* records per popcount 0..166 */
+  int has_tc_fp4;                /* 1 = the FP4 tensor-core operand is resident */
 } fps_library_info;
 
 fps_status fps_library_info_get(fps_library lib, fps_library_info* info);
@@ -129,13 +132,14 @@ fps_status fps_library_cid(fps_library lib, int64_t index, int64_t* cid);
 /* --------------------------------------------------------------- searching */
 
 typedef enum {
-  FPS_PATH_AUTO = 0,     /* batch calls: the first batch of each size class (ceil log2 Q) times the popcount
-                            and tensor-core batch paths and keeps the faster for this library */
+  FPS_PATH_AUTO = 0,     /* batch calls: an autotuner picks the kernel and its tile shape per size class
+                            (see "Autotuning" below) */
   FPS_PATH_POPC = 1,     /* popcount scan: one launch per query (single-query kernel) */
   FPS_PATH_POPC_BATCH = 2, /* popcount scan, many queries per launch */
   FPS_PATH_TC_FP8 = 3,   /* tensor-core contraction on 0/1 FP8 operands */
   FPS_PATH_TC_I8 = 4,    /* INT8 tensor-core contraction: FPS_ERR_UNSUPPORTED on sm_103a (no kind::i8) */
-  FPS_PATH_LEARNED = 5   /* predicted per-query threshold, exact fallback */
+  FPS_PATH_LEARNED = 5,  /* predicted per-query threshold, exact fallback */
+  FPS_PATH_TC_FP4 = 6    /* tensor-core contraction on packed 0/1 FP4 operands (unit block scales) */
 } fps_path;
 
 #define FPS_SEARCH_DEVICE_IO 0x1u /* queries, k, offsets and outputs are device pointers; the call only
@@ -146,9 +150,36 @@ typedef struct {
   int64_t queries;               /* queries served by the call */
   int64_t fallbacks;             /* queries that needed the exact fallback scan */
   int64_t candidates;            /* records accepted under the running bounds (batched paths) */
-  int64_t path_used;             /* fps_path actually run */
+  int64_t path_used;             /* fps_path of the kernel that ran (with FPS_PATH_LEARNED: the batched
+                                    kernel that started from the predicted bounds) */
   int64_t device_fallbacks;      /* of the fallbacks, those re-run inside a batch plan's graph */
+  int64_t tile_param;            /* the tile shape used: library tiles per work item (tensor-core paths)
+                                    or queries per work item (FPS_PATH_POPC_BATCH); 0 otherwise */
 } fps_search_stats;
+
+/*
+ * Autotuning (FPS_PATH_AUTO; the paper has no counterpart).  Batched calls fall
+ * into size classes: ceil(log2 Q), ceil(log2 (max k + 1)), and whether learned
+ * bounds are given.  The first call of a class on a library times, on the
+ * call's own queries, every batched kernel the library holds an operand for
+ * (popcount batch; FP8 and FP4 tensor cores) at its default tile shape, then
+ * the fastest kernel at its other tile shapes (tensor cores: 1/2 and 2 x the
+ * default library tiles per work item; popcount batch: 32, 64 or 128 queries
+ * per work item), and keeps the fastest (kernel, shape) for the class.  Every
+ * candidate returns the same exact results, so the call's results do not
+ * depend on the choice.  When the environment variable FPS_TUNE_CACHE names a
+ * file, choices are read from it (entries keyed by device name, library size
+ * N and class) before tuning, and each new choice is merged into it.
+ */
+#define FPS_TUNE_CLASS_LEN 32
+/* Class name of a batch ("q<ceil log2 Q>-k<ceil log2 (kmax + 1)>-l<0|1>") into out (FPS_TUNE_CLASS_LEN). */
+fps_status fps_tune_class(int Q, int k_max, int learned, char* out);
+/* Host-only access to a cache file: look up / merge one entry.  fps_tune_cache_get returns
+   FPS_ERR_IO when the file or the entry does not exist. */
+fps_status fps_tune_cache_get(const char* path, const char* device, int64_t n, const char* cls, int* fps_path_out,
+                              int* tile_param, double* ms);
+fps_status fps_tune_cache_put(const char* path, const char* device, int64_t n, const char* cls, int fps_path_in,
+                              int tile_param, double ms);
 
 typedef struct {
   int path;                      /* fps_path */

@@ -20,8 +20,10 @@ FPS_BITS, FPS_WORDS, FPS_K_MAX, FPS_NOALLOC_K_MAX = 166, 3, 1920, 128
 (FPS_OK, FPS_ERR_INVALID_ARG, FPS_ERR_IO, FPS_ERR_PARSE, FPS_ERR_BUDGET, FPS_ERR_CUDA, FPS_ERR_TIMEOUT,
  FPS_ERR_OVERFLOW_INTERNAL, FPS_ERR_UNSUPPORTED, FPS_ERR_NOMEM) = range(10)
 FPS_LOAD_ACCEPT_167, FPS_LOAD_NO_BUCKETS, FPS_LOAD_TC_OPERAND, FPS_LOAD_TC_INT8 = 0x1, 0x2, 0x4, 0x8
+FPS_LOAD_TC_FP4 = 0x10
 (FPS_PATH_AUTO, FPS_PATH_POPC, FPS_PATH_POPC_BATCH, FPS_PATH_TC_FP8, FPS_PATH_TC_I8,
- FPS_PATH_LEARNED) = range(6)
+ FPS_PATH_LEARNED, FPS_PATH_TC_FP4) = range(7)
+FPS_TUNE_CLASS_LEN = 32
 FPS_SEARCH_DEVICE_IO = 0x1
 
 if not os.path.exists(_SO):
@@ -47,12 +49,12 @@ class fps_load_desc(ctypes.Structure):
 class fps_library_info(ctypes.Structure):
     _fields_ = [("n_records", ctypes.c_int64), ("n_tiles", ctypes.c_int64), ("device_bytes", ctypes.c_size_t),
                 ("device", ctypes.c_int), ("bucketed", ctypes.c_int), ("has_tc_operand", ctypes.c_int),
-                ("bucket_count", ctypes.c_int64 * (FPS_BITS + 1))]
+                ("bucket_count", ctypes.c_int64 * (FPS_BITS + 1)), ("has_tc_fp4", ctypes.c_int)]
 
 
 class fps_search_stats(ctypes.Structure):
     _fields_ = [("queries", ctypes.c_int64), ("fallbacks", ctypes.c_int64), ("candidates", ctypes.c_int64),
-                ("path_used", ctypes.c_int64), ("device_fallbacks", ctypes.c_int64)]
+                ("path_used", ctypes.c_int64), ("device_fallbacks", ctypes.c_int64), ("tile_param", ctypes.c_int64)]
 
 
 class fps_search_opts(ctypes.Structure):
@@ -94,6 +96,11 @@ _lib.fps_mlp_predict.argtypes = [_vp, _vp, _i32, _vp, _vp]
 _lib.fps_mlp_grad.argtypes = [_vp, _vp, _vp, _i32, ctypes.c_float, _vp, _vp, _vp]
 _lib.fps_mlp_train_step.argtypes = [_vp, _vp, _vp, _i32, ctypes.c_float, ctypes.c_float, _vp, _vp]
 _lib.fps_pack_query.argtypes = [ctypes.c_char_p, _vp]
+_lib.fps_tune_class.argtypes = [_i32, _i32, _i32, ctypes.c_char_p]
+_lib.fps_tune_cache_get.argtypes = [ctypes.c_char_p, ctypes.c_char_p, _i64, ctypes.c_char_p, ctypes.POINTER(_i32),
+                                    ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_double)]
+_lib.fps_tune_cache_put.argtypes = [ctypes.c_char_p, ctypes.c_char_p, _i64, ctypes.c_char_p, _i32, _i32,
+                                    ctypes.c_double]
 _lib.fps_pack_text.argtypes = [_vp, ctypes.c_size_t, ctypes.c_uint32, _vp, _vp, ctypes.c_size_t,
                                ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]
 for _f in ("fps_library_load", "fps_release", "fps_library_info_get", "fps_library_cid", "fps_search",
@@ -191,7 +198,32 @@ def fps_library_info_get(lib: Library) -> dict:
     _check(_lib.fps_library_info_get(lib._h, ctypes.byref(info)), "fps_library_info_get")
     return {"n_records": info.n_records, "n_tiles": info.n_tiles, "device_bytes": info.device_bytes,
             "device": info.device, "bucketed": bool(info.bucketed), "has_tc_operand": bool(info.has_tc_operand),
+            "has_tc_fp4": bool(info.has_tc_fp4),
             "bucket_count": np.array(info.bucket_count[:], np.int64)}
+
+
+def fps_tune_class(Q: int, k_max: int, learned: bool = False) -> str:
+    """Autotuner size class of a batch (see include/fps.h)."""
+    buf = ctypes.create_string_buffer(FPS_TUNE_CLASS_LEN)
+    _check(_lib.fps_tune_class(int(Q), int(k_max), int(bool(learned)), buf), "fps_tune_class")
+    return buf.value.decode()
+
+
+def fps_tune_cache_get(path: str, device: str, n: int, cls: str):
+    """(fps_path, tile_param, ms) of a cache entry, or None when the file or entry does not exist."""
+    p, t, ms = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_double(0.0)
+    st = _lib.fps_tune_cache_get(os.fsencode(path), device.encode(), int(n), cls.encode(), ctypes.byref(p),
+                                 ctypes.byref(t), ctypes.byref(ms))
+    if st == FPS_ERR_IO:
+        return None
+    _check(st, "fps_tune_cache_get")
+    return p.value, t.value, ms.value
+
+
+def fps_tune_cache_put(path: str, device: str, n: int, cls: str, path_code: int, tile_param: int, ms: float):
+    """Merge one autotuner choice into a cache file (created if missing)."""
+    _check(_lib.fps_tune_cache_put(os.fsencode(path), device.encode(), int(n), cls.encode(), int(path_code),
+                                   int(tile_param), float(ms)), "fps_tune_cache_put")
 
 
 def fps_library_cid(lib: Library, index: int) -> int:

@@ -391,8 +391,6 @@ __global__ void __launch_bounds__(kSelThreads) batch_select_kernel(DevLib lib, B
   if (threadIdx.x == 0) b.out_count[q] = k_eff;
 }
 
-constexpr int kQB = 64;
-
 }  // namespace
 
 cudaError_t batch_prepare(const DevLib& lib, const BatchDev& b, int use_pilot, cudaStream_t s) {
@@ -414,18 +412,27 @@ cudaError_t batch_thr_from_tau(const BatchDev& b, const float* tau, cudaStream_t
   return cudaGetLastError();
 }
 
-cudaError_t batch_scan_popc(const DevLib& lib, const BatchDev& b, int num_sms, uint32_t* work, cudaStream_t s) {
-  if (b.Q == 0 || lib.n == 0) return cudaSuccess;
+template <int QB>
+cudaError_t launch_batch_popc(const DevLib& lib, const BatchDev& b, int num_sms, uint32_t* work, cudaStream_t s) {
   const int grid = 2 * num_sms;
-  const int n_groups = (b.Q + kQB - 1) / kQB;
+  const int n_groups = (b.Q + QB - 1) / QB;
   int n_chunks = (8 * grid + n_groups - 1) / n_groups;          // several items per block
   int64_t max_chunks = lib.n_tiles / 64 > 0 ? lib.n_tiles / 64 : 1;  // at least 64 tiles per chunk
   if (n_chunks > max_chunks) n_chunks = static_cast<int>(max_chunks);
   if (n_chunks < 1) n_chunks = 1;
   cudaError_t e = cudaMemsetAsync(work, 0, sizeof(uint32_t), s);
   if (e != cudaSuccess) return e;
-  batch_popc_kernel<kQB><<<grid, 256, 0, s>>>(lib, b, n_groups, n_chunks, work);
+  batch_popc_kernel<QB><<<grid, 256, 0, s>>>(lib, b, n_groups, n_chunks, work);
   return cudaGetLastError();
+}
+
+cudaError_t batch_scan_popc(const DevLib& lib, const BatchDev& b, int num_sms, uint32_t* work, int qb,
+                            cudaStream_t s) {
+  if (b.Q == 0 || lib.n == 0) return cudaSuccess;
+  if (qb <= 0) qb = kPopcBatchDefaultQB;
+  if (qb == 32) return launch_batch_popc<32>(lib, b, num_sms, work, s);
+  if (qb == 128) return launch_batch_popc<128>(lib, b, num_sms, work, s);
+  return launch_batch_popc<64>(lib, b, num_sms, work, s);
 }
 
 cudaError_t batch_select(const DevLib& lib, const BatchDev& b, cudaStream_t s) {

@@ -258,9 +258,11 @@ fps_status build_library(const uint64_t* packed, int64_t n, const int64_t* cids,
   std::vector<uint8_t> popc;
   Layout lay = plan_layout(packed, n, bucketed, &popc);
   const bool want_fp8 = (d->flags & FPS_LOAD_TC_OPERAND) != 0;
+  const bool want_fp4 = (d->flags & FPS_LOAD_TC_FP4) != 0;
   if (d->flags & FPS_LOAD_TC_INT8) return FPS_ERR_UNSUPPORTED;        // sm_103a has no tcgen05 kind::i8
-  if (want_fp8 && !bucketed) return FPS_ERR_UNSUPPORTED;              // tensor tiles need popcount buckets
-  size_t need = lay.bytes + (want_fp8 ? tc_operand_bytes(lay.n_tiles) : 0);
+  if ((want_fp8 || want_fp4) && !bucketed) return FPS_ERR_UNSUPPORTED;   // tensor tiles need popcount buckets
+  size_t need = lay.bytes + (want_fp8 ? tc_operand_bytes(kTcFp8, lay.n_tiles) : 0) +
+                (want_fp4 ? tc_operand_bytes(kTcFp4, lay.n_tiles) : 0);
   if (d->hbm_budget_bytes && need > d->hbm_budget_bytes) return FPS_ERR_BUDGET;
 
   Library* L = new (std::nothrow) Library();
@@ -354,10 +356,11 @@ fps_status build_library(const uint64_t* packed, int64_t n, const int64_t* cids,
   L->dev.n = n;
   L->dev.n_tiles = lay.n_tiles;
   L->dev.bucketed = L->bucketed;
-  if (want_fp8) {
+  for (int fmt : {kTcFp8, kTcFp4}) {
+    if (!(fmt == kTcFp8 ? want_fp8 : want_fp4)) continue;
     void* op = nullptr;
-    st = dev_alloc(L, &op, tc_operand_bytes(lay.n_tiles));
-    if (st == FPS_OK && (tc_pack_library(L->dev, static_cast<uint8_t*>(op), nullptr) != cudaSuccess ||
+    st = dev_alloc(L, &op, tc_operand_bytes(fmt, lay.n_tiles));
+    if (st == FPS_OK && (tc_pack_library(fmt, L->dev, static_cast<uint8_t*>(op), nullptr) != cudaSuccess ||
                          cudaDeviceSynchronize() != cudaSuccess)) {
       cudaGetLastError();
       st = FPS_ERR_CUDA;
@@ -366,7 +369,7 @@ fps_status build_library(const uint64_t* packed, int64_t n, const int64_t* cids,
       free_library(L);
       return st;
     }
-    L->tc_fp8 = static_cast<uint8_t*>(op);
+    (fmt == kTcFp8 ? L->tc_fp8 : L->tc_fp4) = static_cast<uint8_t*>(op);
   }
   *out = L;
   return FPS_OK;
@@ -597,7 +600,8 @@ struct BatchLayout {
   size_t d_thr, d_hist, d_work, d_oi, d_od, d_oc, d_cnt, d_cand, out_begin, out_end, d_qop, bytes;
 };
 
-BatchLayout batch_layout(int Q, int64_t total, int64_t cand_keys, bool dev_io, bool learned, bool tc) {
+// qop_bytes: the tensor-core query operand (0 for the popcount batch)
+BatchLayout batch_layout(int Q, int64_t total, int64_t cand_keys, bool dev_io, bool learned, size_t qop_bytes) {
   BatchLayout l{};
   Carve dv;
   l.d_q = dv.take(dev_io ? 0 : sizeof(uint64_t) * 3 * Q);
@@ -616,7 +620,7 @@ BatchLayout batch_layout(int Q, int64_t total, int64_t cand_keys, bool dev_io, b
   l.d_cand = dv.take(sizeof(unsigned long long) * static_cast<size_t>(cand_keys));
   l.out_begin = dev_io ? l.d_oc : l.d_oi;
   l.out_end = l.d_cand;
-  l.d_qop = dv.take(tc ? tc_query_operand_bytes(Q) : 0);
+  l.d_qop = dv.take(qop_bytes);
   l.bytes = dv.at;
   return l;
 }
@@ -656,18 +660,33 @@ BatchDev batch_dev(char* db, const BatchLayout& l, int Q, const uint64_t* dev_qu
   return b;
 }
 
+bool is_tc_path(int path) { return path == FPS_PATH_TC_FP8 || path == FPS_PATH_TC_FP4; }
+int tc_fmt_of(int path) { return path == FPS_PATH_TC_FP4 ? kTcFp4 : kTcFp8; }
+const uint8_t* tc_operand_of(const Library* L, int path) {
+  return path == FPS_PATH_TC_FP4 ? L->tc_fp4 : (path == FPS_PATH_TC_FP8 ? L->tc_fp8 : nullptr);
+}
+size_t qop_bytes_of(int path, int Q) { return is_tc_path(path) ? tc_query_operand_bytes(tc_fmt_of(path), Q) : 0; }
+// The tile parameter a batched path runs with (param <= 0: its default).
+int tile_param_of(int path, int param) {
+  if (param > 0) return param;
+  if (is_tc_path(path)) return tc_default_chunk(tc_fmt_of(path));
+  return path == FPS_PATH_POPC_BATCH ? kPopcBatchDefaultQB : 0;
+}
+
 // The device work of one batch: bounds (sampled or predicted), scan, per-query select.
-cudaError_t enqueue_batch(Library* L, const BatchDev& b, char* db, const BatchLayout& l, bool tc,
+// path: FPS_PATH_POPC_BATCH, FPS_PATH_TC_FP8 or FPS_PATH_TC_FP4; param: its tile parameter.
+cudaError_t enqueue_batch(Library* L, const BatchDev& b, char* db, const BatchLayout& l, int path, int param,
                           const float* tau_dev, double tmo, cudaStream_t s) {
   cudaError_t ce = batch_prepare(L->dev, b, tau_dev ? 0 : 1, s);
   if (ce == cudaSuccess && tau_dev) ce = batch_thr_from_tau(b, tau_dev, s);
   if (ce == cudaSuccess) {
-    if (tc) {
+    if (is_tc_path(path)) {
+      const int fmt = tc_fmt_of(path);
       uint8_t* qop = reinterpret_cast<uint8_t*>(db + l.d_qop);
-      ce = tc_pack_queries(b.queries, b.Q, qop, s);
-      if (ce == cudaSuccess) ce = tc_scan(L->dev, b, L->tc_fp8, qop, L->num_sms, tmo, s);
+      ce = tc_pack_queries(fmt, b.queries, b.Q, qop, s);
+      if (ce == cudaSuccess) ce = tc_scan(fmt, L->dev, b, tc_operand_of(L, path), qop, L->num_sms, param, tmo, s);
     } else {
-      ce = batch_scan_popc(L->dev, b, L->num_sms, reinterpret_cast<uint32_t*>(db + l.d_work), s);
+      ce = batch_scan_popc(L->dev, b, L->num_sms, reinterpret_cast<uint32_t*>(db + l.d_work), param, s);
     }
   }
   if (ce == cudaSuccess) ce = batch_select(L->dev, b, s);
@@ -729,14 +748,13 @@ fps_status finish_batch(Library* L, Workspace* w, const char* hb, const char* db
 }
 
 // Many queries per launch with the batched kernels (bounds, scan, per-query select).
-fps_status batch_kernels(Library* L, Workspace* w, int path, const uint64_t* queries, int Q, const int32_t* k,
-                         const int64_t* off, int64_t total, int32_t* out_index, int32_t* out_dist,
+fps_status batch_kernels(Library* L, Workspace* w, int path, int param, const uint64_t* queries, int Q,
+                         const int32_t* k, const int64_t* off, int64_t total, int32_t* out_index, int32_t* out_dist,
                          int32_t* out_count, const fps_search_opts* opts, bool dev_io, cudaStream_t s,
                          int64_t* n_fallback, const float* learned_tau) {
-  const bool tc = path == FPS_PATH_TC_FP8;
   const bool learned = learned_tau != nullptr;
   std::vector<int64_t> coff = batch_cand_offsets(k, Q, L->n);
-  const BatchLayout l = batch_layout(Q, total, coff[Q], dev_io, learned, tc);
+  const BatchLayout l = batch_layout(Q, total, coff[Q], dev_io, learned, qop_bytes_of(path, Q));
   fps_status st = batch_staging(w, l.bytes, l.plan_end > l.out_end ? l.plan_end : l.out_end);
   if (st != FPS_OK) return st;
   char* db = static_cast<char*>(w->batch_block);
@@ -749,7 +767,7 @@ fps_status batch_kernels(Library* L, Workspace* w, int path, const uint64_t* que
   const BatchDev b = batch_dev(db, l, Q, dev_io ? queries : nullptr, dev_io ? out_index : nullptr,
                                dev_io ? out_dist : nullptr, &w->io->err);
   const float* tau_dev = learned ? (dev_io ? learned_tau : reinterpret_cast<const float*>(db + l.d_tau)) : nullptr;
-  if (enqueue_batch(L, b, db, l, tc, tau_dev, opt_timeout(opts), s) != cudaSuccess) {
+  if (enqueue_batch(L, b, db, l, path, param, tau_dev, opt_timeout(opts), s) != cudaSuccess) {
     cudaGetLastError();
     return FPS_ERR_CUDA;
   }
@@ -766,89 +784,17 @@ fps_status batch_kernels(Library* L, Workspace* w, int path, const uint64_t* que
                       n_fallback);
 }
 
-fps_status search_batch_impl(Library* L, const uint64_t* queries, int Q, const int32_t* k, const int64_t* off,
-                             int64_t total, int32_t* out_index, int32_t* out_dist, int32_t* out_count,
-                             const fps_search_opts* opts, bool dev_io, cudaStream_t s) {
-  if (Q == 0) return FPS_OK;
-  Workspace* w = nullptr;
-  fps_status st = get_workspace(L, s, &w);
-  if (st != FPS_OK) return st;
-  const double tmo = opt_timeout(opts);
-  int path = opts ? opts->path : FPS_PATH_AUTO;
-  const float* tau = nullptr;
-  if (path == FPS_PATH_LEARNED) {
-    if (!opts->tau) return FPS_ERR_INVALID_ARG;
-    tau = opts->tau;                      // predicted bounds replace the pilot; the scan itself is chosen below
-    path = FPS_PATH_AUTO;
-  }
-  if (path == FPS_PATH_AUTO && !L->tc_fp8) path = FPS_PATH_POPC_BATCH;
-  if (path == FPS_PATH_AUTO) {
-    // autotuner: the first batch of a size class runs both batched paths (identical, exact
-    // results) and the faster one is kept for that class of this library
-    int cls = 0;
-    while ((1 << cls) < Q) ++cls;
-    cls = cls * 2 + (tau ? 1 : 0);
-    int chosen = -1;
-    {
-      std::lock_guard<std::mutex> lock(L->mu);
-      auto it = L->tuned.find(cls);
-      if (it != L->tuned.end()) chosen = it->second;
-    }
-    if (chosen < 0) {
-      if (!dev_io)
-        for (int q = 0; q < Q; ++q)
-          if (queries[3 * q + 2] >> (kBits - 128)) return FPS_ERR_INVALID_ARG;
-      int64_t nf = 0;
-      auto t0 = std::chrono::steady_clock::now();
-      st = batch_kernels(L, w, FPS_PATH_POPC_BATCH, queries, Q, k, off, total, out_index, out_dist, out_count, opts,
-                         dev_io, s, &nf, tau);
-      if (st != FPS_OK) return st;
-      auto t1 = std::chrono::steady_clock::now();
-      st = batch_kernels(L, w, FPS_PATH_TC_FP8, queries, Q, k, off, total, out_index, out_dist, out_count, opts,
-                         dev_io, s, &nf, tau);
-      if (st != FPS_OK) return st;
-      auto t2 = std::chrono::steady_clock::now();
-      chosen = (t2 - t1) < (t1 - t0) ? FPS_PATH_TC_FP8 : FPS_PATH_POPC_BATCH;
-      {
-        std::lock_guard<std::mutex> lock(L->mu);
-        L->tuned[cls] = chosen;
-      }
-      if (opts && opts->stats) {
-        opts->stats->queries = Q;
-        opts->stats->fallbacks = nf;
-        opts->stats->device_fallbacks = 0;
-        opts->stats->path_used = tau ? FPS_PATH_LEARNED : FPS_PATH_TC_FP8;
-      }
-      return FPS_OK;
-    }
-    path = chosen;
-  }
-  if (path == FPS_PATH_TC_FP8 && !L->tc_fp8) return FPS_ERR_UNSUPPORTED;
-  if (path != FPS_PATH_POPC) {
-    if (path != FPS_PATH_POPC_BATCH && path != FPS_PATH_TC_FP8) return FPS_ERR_UNSUPPORTED;  // TC_I8: no kind::i8
-    if (!dev_io)
-      for (int q = 0; q < Q; ++q)
-        if (queries[3 * q + 2] >> (kBits - 128)) return FPS_ERR_INVALID_ARG;
-    int64_t nf = 0;
-    st = batch_kernels(L, w, path, queries, Q, k, off, total, out_index, out_dist, out_count, opts, dev_io, s, &nf,
-                       tau);
-    if (st == FPS_OK && opts && opts->stats) {
-      opts->stats->queries = Q;
-      opts->stats->fallbacks = nf;
-      opts->stats->device_fallbacks = 0;
-      opts->stats->path_used = tau ? FPS_PATH_LEARNED : path;
-    }
-    return st;
-  }
+// Queries one after another through the single-query scan (FPS_PATH_POPC), host or device form.
+fps_status run_sequential(Library* L, Workspace* w, const uint64_t* queries, int Q, const int32_t* k,
+                          const int64_t* off, int64_t total, int32_t* out_index, int32_t* out_dist,
+                          int32_t* out_count, double tmo, bool dev_io, cudaStream_t s) {
   if (dev_io) return batch_sequential(L, w, queries, Q, k, off, out_index, out_dist, out_count, tmo, s);
-  for (int q = 0; q < Q; ++q)
-    if (queries[3 * q + 2] >> (kBits - 128)) return FPS_ERR_INVALID_ARG;
   // device staging: [queries Q*3][index total][dist total][count Q]; host mirror of the same
   const size_t qb = static_cast<size_t>(Q) * 3 * sizeof(uint64_t);
   const size_t rb = static_cast<size_t>(total) * sizeof(int32_t);
   const size_t cb = static_cast<size_t>(Q) * sizeof(int32_t);
   const size_t bytes = qb + 2 * rb + cb;
-  st = batch_staging(w, bytes, bytes);
+  fps_status st = batch_staging(w, bytes, bytes);
   if (st != FPS_OK) return st;
   char* hb = static_cast<char*>(w->batch_host);
   char* db = static_cast<char*>(w->batch_block);
@@ -878,14 +824,170 @@ fps_status search_batch_impl(Library* L, const uint64_t* queries, int Q, const i
     std::memcpy(out_dist + off[q], hd + off[q], sizeof(int32_t) * hc[q]);
     fill_unused(out_index + off[q], out_dist + off[q], hc[q], k[q]);
   }
-  if (opts && opts->stats) {
-    opts->stats->queries = Q;
-    opts->stats->fallbacks = 0;
-    opts->stats->device_fallbacks = 0;
-    opts->stats->candidates = 0;
-    opts->stats->path_used = FPS_PATH_POPC;
-  }
   return FPS_OK;
+}
+
+bool path_available(const Library* L, int path) {
+  if (path == FPS_PATH_POPC || path == FPS_PATH_POPC_BATCH) return true;
+  return tc_operand_of(L, path) != nullptr;
+}
+
+// One call on a resolved path (FPS_PATH_POPC, _POPC_BATCH, _TC_FP8 or _TC_FP4) with its
+// tile parameter; *n_fallback counts the queries re-run by the exact single-query scan.
+fps_status run_path(Library* L, Workspace* w, int path, int param, const uint64_t* queries, int Q, const int32_t* k,
+                    const int64_t* off, int64_t total, int32_t* out_index, int32_t* out_dist, int32_t* out_count,
+                    const fps_search_opts* opts, bool dev_io, cudaStream_t s, const float* tau,
+                    int64_t* n_fallback) {
+  *n_fallback = 0;
+  if (path == FPS_PATH_POPC)
+    return run_sequential(L, w, queries, Q, k, off, total, out_index, out_dist, out_count, opt_timeout(opts), dev_io,
+                          s);
+  return batch_kernels(L, w, path, param, queries, Q, k, off, total, out_index, out_dist, out_count, opts, dev_io, s,
+                       n_fallback, tau);
+}
+
+std::string device_name(int device) {
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
+    cudaGetLastError();
+    return "unknown";
+  }
+  return prop.name;
+}
+
+// Autotuner (FPS_PATH_AUTO): every batched kernel the library holds an operand for at
+// its default tile shape (and, for at most 64 queries, the sequential single-query
+// scan), then the fastest kernel at its other tile shapes; each run is the whole call
+// and returns the same exact results, so the call's outputs are those of the last run.
+fps_status autotune(Library* L, Workspace* w, const std::string& cls, const uint64_t* queries, int Q, const int32_t* k,
+                    const int64_t* off, int64_t total, int32_t* out_index, int32_t* out_dist, int32_t* out_count,
+                    const fps_search_opts* opts, bool dev_io, cudaStream_t s, const float* tau,
+                    Library::Choice* chosen, int64_t* n_fallback) {
+  std::vector<Library::Choice> cands;
+  if (Q <= 64) cands.push_back({FPS_PATH_POPC, 0});
+  for (int p : {FPS_PATH_POPC_BATCH, FPS_PATH_TC_FP8, FPS_PATH_TC_FP4})
+    if (path_available(L, p)) cands.push_back({p, tile_param_of(p, 0)});
+  double best_ms = 0.0;
+  auto timed = [&](const Library::Choice& c) -> fps_status {
+    int64_t nf = 0;
+    auto t0 = std::chrono::steady_clock::now();
+    fps_status st = run_path(L, w, c.path, c.param, queries, Q, k, off, total, out_index, out_dist, out_count, opts,
+                             dev_io, s, tau, &nf);
+    if (st == FPS_OK && cudaStreamSynchronize(s) != cudaSuccess) {
+      cudaGetLastError();
+      st = FPS_ERR_CUDA;
+    }
+    if (st != FPS_OK) return st;
+    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (chosen->path == 0 || ms < best_ms) {
+      *chosen = c;
+      best_ms = ms;
+      *n_fallback = nf;
+    }
+    return FPS_OK;
+  };
+  *chosen = Library::Choice{};
+  for (const auto& c : cands) {
+    fps_status st = timed(c);
+    if (st != FPS_OK) return st;
+  }
+  std::vector<int> shapes;
+  if (chosen->path == FPS_PATH_POPC_BATCH) shapes = {32, 128};
+  if (is_tc_path(chosen->path)) {
+    const int d = tc_default_chunk(tc_fmt_of(chosen->path));
+    shapes = {d / 2, 2 * d};
+  }
+  const int best_path = chosen->path;
+  for (int p : shapes) {
+    fps_status st = timed({best_path, p});
+    if (st != FPS_OK) return st;
+  }
+  {
+    std::lock_guard<std::mutex> lock(L->mu);
+    L->tuned[cls] = *chosen;
+  }
+  const char* cache = std::getenv("FPS_TUNE_CACHE");
+  if (cache && *cache) tune_cache_put(cache, device_name(L->device).c_str(), L->n, cls, chosen->path, chosen->param,
+                                      best_ms);
+  return FPS_OK;
+}
+
+fps_status search_batch_impl(Library* L, const uint64_t* queries, int Q, const int32_t* k, const int64_t* off,
+                             int64_t total, int32_t* out_index, int32_t* out_dist, int32_t* out_count,
+                             const fps_search_opts* opts, bool dev_io, cudaStream_t s) {
+  if (Q == 0) return FPS_OK;
+  Workspace* w = nullptr;
+  fps_status st = get_workspace(L, s, &w);
+  if (st != FPS_OK) return st;
+  int path = opts ? opts->path : FPS_PATH_AUTO;
+  const float* tau = nullptr;
+  if (path == FPS_PATH_LEARNED) {
+    if (!opts->tau) return FPS_ERR_INVALID_ARG;
+    tau = opts->tau;                      // predicted bounds replace the pilot; the scan itself is tuned below
+    path = FPS_PATH_AUTO;
+  }
+  if (!dev_io)
+    for (int q = 0; q < Q; ++q)
+      if (queries[3 * q + 2] >> (kBits - 128)) return FPS_ERR_INVALID_ARG;
+  int param = 0;
+  int64_t nf = 0;
+  if (path == FPS_PATH_AUTO) {
+    int kmax = 0;
+    for (int q = 0; q < Q; ++q) kmax = std::max(kmax, k[q]);
+    const std::string cls = tune_class_name(Q, kmax, tau != nullptr);
+    Library::Choice c{};
+    bool known = false;
+    {
+      std::lock_guard<std::mutex> lock(L->mu);
+      auto it = L->tuned.find(cls);
+      if (it != L->tuned.end()) {
+        c = it->second;
+        known = true;
+      }
+    }
+    const char* cache = std::getenv("FPS_TUNE_CACHE");
+    if (!known && cache && *cache) {
+      int cp = 0, cparam = 0;
+      double ms = 0.0;
+      if (tune_cache_get(cache, device_name(L->device).c_str(), L->n, cls, &cp, &cparam, &ms) &&
+          path_available(L, cp) && (cp == FPS_PATH_POPC ? Q <= 64 : cp != FPS_PATH_AUTO)) {
+        c = {cp, cparam};
+        known = true;
+        std::lock_guard<std::mutex> lock(L->mu);
+        L->tuned[cls] = c;
+      }
+    }
+    if (!known) {
+      st = autotune(L, w, cls, queries, Q, k, off, total, out_index, out_dist, out_count, opts, dev_io, s, tau, &c,
+                    &nf);
+      if (st != FPS_OK) return st;
+      if (opts && opts->stats) {
+        opts->stats->queries = Q;
+        opts->stats->fallbacks = nf;
+        opts->stats->device_fallbacks = 0;
+        opts->stats->path_used = c.path;
+        opts->stats->tile_param = c.param;
+      }
+      return FPS_OK;
+    }
+    path = c.path;
+    param = c.param;
+  }
+  if (path != FPS_PATH_POPC && path != FPS_PATH_POPC_BATCH && !is_tc_path(path))
+    return FPS_ERR_UNSUPPORTED;   // FPS_PATH_TC_I8: sm_103a has no kind::i8
+  if (!path_available(L, path)) return FPS_ERR_UNSUPPORTED;
+  param = path == FPS_PATH_POPC ? 0 : tile_param_of(path, param);
+  st = run_path(L, w, path, param, queries, Q, k, off, total, out_index, out_dist, out_count, opts, dev_io, s, tau,
+                &nf);
+  if (st == FPS_OK && opts && opts->stats) {
+    opts->stats->queries = Q;
+    opts->stats->fallbacks = nf;
+    opts->stats->device_fallbacks = 0;
+    if (path == FPS_PATH_POPC) opts->stats->candidates = 0;
+    opts->stats->path_used = path;
+    opts->stats->tile_param = param;
+  }
+  return st;
 }
 
 // A batch whose shape (Q, k, path) is fixed: own buffers and one captured CUDA
@@ -893,7 +995,8 @@ fps_status search_batch_impl(Library* L, const uint64_t* queries, int Q, const i
 struct BatchPlan {
   Library* L = nullptr;
   int Q = 0;
-  bool tc = false, learned = false;
+  int path = FPS_PATH_POPC_BATCH, param = 0;   // batched kernel and its tile parameter
+  bool learned = false;
   std::vector<int32_t> k;
   std::vector<int64_t> off, coff;
   int64_t total = 0;
@@ -980,7 +1083,7 @@ cudaError_t plan_enqueue(BatchPlan* P, double tmo, cudaStream_t s, bool captured
   const BatchDev b = batch_dev(P->db, P->lay, P->Q, nullptr, nullptr, nullptr, P->err);
   const float* tau_dev = P->learned ? reinterpret_cast<const float*>(P->db + P->lay.d_tau) : nullptr;
   cudaError_t e = cudaMemcpyAsync(P->db, P->hb, P->lay.plan_end, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = enqueue_batch(P->L, b, P->db, P->lay, P->tc, tau_dev, tmo, s);
+  if (e == cudaSuccess) e = enqueue_batch(P->L, b, P->db, P->lay, P->path, P->param, tau_dev, tmo, s);
   if (e == cudaSuccess && captured) e = plan_capture_fallback(P, tmo, s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(P->hb + P->lay.out_begin, P->db + P->lay.out_begin, P->lay.out_end - P->lay.out_begin,
@@ -1102,6 +1205,7 @@ fps_status fps_library_info_get(fps_library lib, fps_library_info* info) {
   info->device = L->device;
   info->bucketed = L->bucketed;
   info->has_tc_operand = L->tc_fp8 ? 1 : 0;
+  info->has_tc_fp4 = L->tc_fp4 ? 1 : 0;
   for (int b = 0; b < kNumBuckets; ++b) info->bucket_count[b] = L->bucket_count[b];
   return FPS_OK;
 }
@@ -1524,14 +1628,31 @@ fps_status fps_batch_plan_create(fps_library lib, int Q, const int32_t* k, int p
   if (!lib || !out || Q <= 0 || !k) return FPS_ERR_INVALID_ARG;
   *out = nullptr;
   Library* L = reinterpret_cast<Library*>(lib);
-  if (path == FPS_PATH_AUTO) path = L->tc_fp8 ? FPS_PATH_TC_FP8 : FPS_PATH_POPC_BATCH;
-  if (path != FPS_PATH_POPC_BATCH && path != FPS_PATH_TC_FP8) return FPS_ERR_UNSUPPORTED;
-  if (path == FPS_PATH_TC_FP8 && !L->tc_fp8) return FPS_ERR_UNSUPPORTED;
+  int param = 0;
+  if (path == FPS_PATH_AUTO) {
+    // the batched kernel the autotuner chose for this size class, if it chose one already;
+    // else the tensor cores when the library holds an operand for them
+    int kmax = 0;
+    for (int q = 0; q < Q; ++q) kmax = std::max(kmax, k[q]);
+    {
+      std::lock_guard<std::mutex> lock(L->mu);
+      auto it = L->tuned.find(tune_class_name(Q, kmax, learned != 0));
+      if (it != L->tuned.end() && it->second.path != FPS_PATH_POPC) {
+        path = it->second.path;
+        param = it->second.param;
+      }
+    }
+    if (path == FPS_PATH_AUTO)
+      path = L->tc_fp8 ? FPS_PATH_TC_FP8 : (L->tc_fp4 ? FPS_PATH_TC_FP4 : FPS_PATH_POPC_BATCH);
+  }
+  if (path != FPS_PATH_POPC_BATCH && !is_tc_path(path)) return FPS_ERR_UNSUPPORTED;
+  if (!path_available(L, path)) return FPS_ERR_UNSUPPORTED;
   BatchPlan* P = new (std::nothrow) BatchPlan();
   if (!P) return FPS_ERR_NOMEM;
   P->L = L;
   P->Q = Q;
-  P->tc = path == FPS_PATH_TC_FP8;
+  P->path = path;
+  P->param = tile_param_of(path, param);
   P->learned = learned != 0;
   P->k.assign(k, k + Q);
   P->off.assign(static_cast<size_t>(Q) + 1, 0);
@@ -1545,7 +1666,7 @@ fps_status fps_batch_plan_create(fps_library lib, int Q, const int32_t* k, int p
   }
   P->total = P->off[Q];
   P->coff = batch_cand_offsets(k, Q, L->n);
-  P->lay = batch_layout(Q, P->total, P->coff[Q], false, P->learned, P->tc);
+  P->lay = batch_layout(Q, P->total, P->coff[Q], false, P->learned, qop_bytes_of(P->path, Q));
   DeviceGuard g(L->device);
   const size_t hbytes = P->lay.plan_end > P->lay.out_end ? P->lay.plan_end : P->lay.out_end;
   if (!g.ok || cudaMalloc(&P->db, P->lay.bytes) != cudaSuccess || cudaMallocHost(&P->hb, hbytes) != cudaSuccess ||
@@ -1635,7 +1756,8 @@ fps_status fps_batch_plan_run(fps_batch_plan plan, const uint64_t* queries, cons
     stats->queries = P->Q;
     stats->fallbacks = nf + *P->fb_count_host;
     stats->device_fallbacks = *P->fb_count_host;
-    stats->path_used = P->learned ? FPS_PATH_LEARNED : (P->tc ? FPS_PATH_TC_FP8 : FPS_PATH_POPC_BATCH);
+    stats->path_used = P->path;
+    stats->tile_param = P->param;
   }
   return st;
 }

@@ -9,6 +9,7 @@
 #include <cstdint>
 #include <map>
 #include <mutex>
+#include <string>
 #include <vector>
 
 #include "fps.h"
@@ -124,7 +125,15 @@ struct Library {
   std::mutex mu;
   std::map<cudaStream_t, Workspace*> ws;
   uint8_t* tc_fp8 = nullptr;     // 0/1 FP8 operand (tensor-core path), or null
-  std::map<int, int> tuned;      // autotuner: batch size class -> fastest batched path
+  uint8_t* tc_fp4 = nullptr;     // packed 0/1 FP4 operand (tensor-core path), or null
+  // autotuner: size class -> fastest (batched path, tile parameter); the cache file's
+  // entries for this library are read once, on the first tuned call
+  struct Choice {
+    int path = 0;
+    int param = 0;
+  };
+  std::map<std::string, Choice> tuned;
+  bool tune_cache_read = false;
 };
 
 // Per-query state of a batched search (device pointers; fps_batch.cu).
@@ -154,8 +163,10 @@ struct BatchDev {
 cudaError_t batch_prepare(const DevLib& lib, const BatchDev& b, int use_pilot, cudaStream_t s);
 // Starting bounds from predicted distances: thr[q] = clamp(ceil(tau[q]), 0, 166).
 cudaError_t batch_thr_from_tau(const BatchDev& b, const float* tau, cudaStream_t s);
-cudaError_t batch_scan_popc(const DevLib& lib, const BatchDev& b, int num_sms, uint32_t* work_counter,
+// qb: queries per work item, 32, 64 or 128 (<= 0: the default, 64)
+cudaError_t batch_scan_popc(const DevLib& lib, const BatchDev& b, int num_sms, uint32_t* work_counter, int qb,
                             cudaStream_t s);
+constexpr int kPopcBatchDefaultQB = 64;
 cudaError_t batch_select(const DevLib& lib, const BatchDev& b, cudaStream_t s);
 
 // ---- shard merge (fps_batch.cu): per-shard result lists of one batch (device memory, laid out
@@ -209,13 +220,28 @@ cudaError_t cluster_final_assign(const ClusterRounds& r, cudaStream_t s);
 cudaError_t cluster_silhouette(const int32_t* D, int Q, const int32_t* lab, int c, int32_t* sizes,
                                unsigned long long* score, cudaStream_t s);
 
+// ---- autotuner: size classes and the JSON cache of chosen kernels and tile shapes (fps_tune.cpp)
+std::string tune_class_name(int Q, int k_max, bool learned);
+bool tune_cache_get(const char* path, const char* device, int64_t n, const std::string& cls, int* path_out,
+                    int* param, double* ms);
+bool tune_cache_put(const char* path, const char* device, int64_t n, const std::string& cls, int path_in, int param,
+                    double ms);
+
 // ---- tensor-core batched scan (fps_tc.cu)
-size_t tc_operand_bytes(int64_t n_tiles128);
-size_t tc_query_operand_bytes(int Q);
-cudaError_t tc_pack_library(const DevLib& lib, uint8_t* op, cudaStream_t s);
-cudaError_t tc_pack_queries(const uint64_t* q, int Q, uint8_t* op, cudaStream_t s);
-cudaError_t tc_scan(const DevLib& lib, const BatchDev& b, const uint8_t* lib_op, const uint8_t* q_op, int num_sms,
-                    double timeout_s, cudaStream_t s);
+// Operand formats: 0/1 FP8 E4M3 bytes (kind::f8f6f4, 256-record tiles) or packed
+// FP4 E2M1 nibbles with unit block scales (kind::mxf4, 192-record tiles).
+constexpr int kTcFp8 = 0;
+constexpr int kTcFp4 = 1;
+int64_t tc_tiles(int fmt, int64_t n_tiles128);         // library tiles of the format
+int tc_tile_rows(int fmt);                              // records per library tile
+size_t tc_operand_bytes(int fmt, int64_t n_tiles128);
+size_t tc_query_operand_bytes(int fmt, int Q);
+cudaError_t tc_pack_library(int fmt, const DevLib& lib, uint8_t* op, cudaStream_t s);
+cudaError_t tc_pack_queries(int fmt, const uint64_t* q, int Q, uint8_t* op, cudaStream_t s);
+// chunk: library tiles per work item (<= 0: the format's default)
+cudaError_t tc_scan(int fmt, const DevLib& lib, const BatchDev& b, const uint8_t* lib_op, const uint8_t* q_op,
+                    int num_sms, int chunk, double timeout_s, cudaStream_t s);
+int tc_default_chunk(int fmt);
 
 // Description of one search for the indirect scan launch (device memory).  The device-side
 // fallback of a captured batch fills it for each query it re-runs; cursor and nfallback are

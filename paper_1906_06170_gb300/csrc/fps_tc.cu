@@ -4,30 +4,35 @@
 //   d(q, x) = sum_j |q_j - x_j| = popc(q) + popc(x) - 2 (q . x),
 // so a batch of queries against the library is one dense contraction
 // Q x K x N (K = 166 keys, padded to 192) followed by a per-element compare.
-// Operands are 0/1 bytes in FP8 E4M3 (0x38 = 1.0, 0x00 = 0) and the
-// accumulators FP16.  Every product is 0 or 1 and every partial sum an integer
-// <= 166, which FP16 represents exactly (all integers up to 2048), so the
-// accumulator is the exact integer q . x and the distances equal the popcount
-// path's.  (sm_103a has no tcgen05 kind::i8, so there is no INT8 variant.)
+// Every product is 0 or 1 and every partial sum an integer <= 166, so any
+// accumulator that holds the integers up to 166 exactly gives the exact q . x,
+// and the distances equal the popcount path's.  Two operand formats:
+//   FP8  kind::f8f6f4, E4M3 bytes (0x38 = 1.0), FP16 accumulators (every
+//        integer up to 2048 is exact in FP16); tiles of 256 records;
+//   FP4  kind::mxf4 (block-scaled), packed E2M1 nibbles (0x2 = 1.0, two keys
+//        per byte), FP32 accumulators; every UE8M0 scale factor is 127
+//        (2^0 = 1), so each product is still 0 or 1; tiles of 192 records,
+//        because the scale factors need TMEM columns next to the two
+//        accumulators.  Half the operand bytes of FP8 per key.
+// (sm_103a has no tcgen05 kind::i8, so there is no INT8 variant.)
 //
 // CTA (one per SM, 13 warps):
 //   warp 0  producer: 1-D bulk copies (cp.async.bulk) of the query tile A
-//           (128 x 192 B, double-buffered per work item) and of library tiles B
-//           (256 x 192 B = 48 KB) into a 3-stage ring, completing on mbarriers;
-//   warp 1  allocates 512 TMEM columns; one thread issues 6 tcgen05.mma
-//           (kind::f8f6f4, K = 32 each) per library tile into one of two
-//           256-column FP16 accumulators and commits to the stage-free and
+//           (128 rows, double-buffered per work item) and of library tiles B
+//           into a ring of stages, completing on mbarriers;
+//   warp 1  allocates 512 TMEM columns; one thread issues the MMAs of a
+//           library tile (K = 192 in slices of 32 (FP8) or 64 (FP4) keys) into
+//           one of two accumulators and commits to the stage-free and
 //           accumulator-full barriers;
 //   warps 2..9 epilogue: thread = query (TMEM lane), two warps per lane
-//           quarter, each reading 128 of the 256 columns with two tcgen05.ld
-//           (pack::16b: two FP16 columns per register) and one wait.  The
-//           accumulator goes back to the MMA as soon as the values are in
-//           registers.  The test needs one number per (query, tile), because a
-//           tile lies inside one popcount bucket:
+//           quarter, each reading half of the tile's columns (tcgen05.ld) with
+//           one wait.  The accumulator goes back to the MMA as soon as the
+//           values are in registers.  The test needs one number per (query,
+//           group of columns), because a group lies inside one popcount bucket:
 //             d <= thr  <=>  acc >= ceil((popc q + popc x - thr) / 2),
-//           taken as a 3-input max over the FP16 bit patterns (non-negative
-//           FP16 values order like unsigned integers) per 64 columns.  A lane
-//           whose 64 columns pass hands them, with the bar, to a shared ring;
+//           taken as a max over the groups' bit patterns (non-negative FP16
+//           and FP32 values order like unsigned integers).  A lane whose group
+//           passes hands it (as FP16), with the bar, to a shared ring;
 //   warps 10, 11 flushers, taking alternate 32-slot blocks of the ring: each
 //           finishes the compare of up to 32 ring entries per round (one lane
 //           per entry, 64 columns), takes each entry's candidate slots with one
@@ -42,11 +47,11 @@
 //           epilogue through a per-row shared word.
 // Operand layout (both operands, K-major, no swizzle): 8-row x 16-byte core
 // matrices of 128 contiguous bytes; along K they follow each other (leading
-// byte offset 128), along rows every 8-row group spans all 12 K-chunks (stride
-// byte offset 1536).  The library operand is written in exactly this layout at
-// load time, so a plain bulk copy lands a tile ready for the MMA.
-// Work: items (query tile, 64-tile library chunk) in chunk-major order, dealt
-// round-robin, so the 32 query tiles of a chunk run at the same time and the
+// byte offset 128), along rows every 8-row group spans all K chunks (stride
+// byte offset 128 x chunks).  The library operand is written in exactly this
+// layout at load time, so a plain bulk copy lands a tile ready for the MMA.
+// Work: items (query tile, chunk of library tiles) in chunk-major order, dealt
+// round-robin, so the query tiles of a chunk run at the same time and the
 // chunk is read from HBM once and from L2 by the rest.
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -59,16 +64,9 @@ namespace fps {
 namespace {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
-constexpr int kTcRows = 256;                 // library records per tensor tile (N)
 constexpr int kTcQ = 128;                    // queries per CTA (M)
-constexpr int kKBytes = 192;                 // 166 keys padded to 6 x 32
-constexpr int kSbo = 1536;                   // bytes between 8-row groups
 constexpr int kLbo = 128;                    // bytes between 16-byte K chunks
-constexpr int kBTileBytes = kTcRows * kKBytes;   // 49152
-constexpr int kATileBytes = kTcQ * kKBytes;      // 24576
-constexpr int kBStages = 3;
-constexpr int kChunkTiles = 64;              // library tiles per work item
-constexpr int kEpiWarps = 8;                 // two per TMEM lane quarter, 128 columns each
+constexpr int kEpiWarps = 8;                 // two per TMEM lane quarter
 constexpr int kFlushWarps = 2;               // drain the hand-off ring, alternate 32-slot blocks
 constexpr int kFlushWarp0 = 2 + kEpiWarps;   // first flusher
 constexpr int kRefWarp = kFlushWarp0 + kFlushWarps;   // re-derives query bounds from the histograms
@@ -77,6 +75,43 @@ constexpr uint32_t kRefCap = 32;             // pending bound refreshes per flus
 constexpr uint32_t kRingCap = 192;           // epilogue hand-offs in flight per CTA
 static_assert(kRingCap % (32 * kFlushWarps) == 0, "ring blocks alternate between the flushers");
 constexpr uint32_t kTmemCols = 512;
+
+// Operand formats.  kRows = records per library tile (the MMA's N), kKBytes =
+// operand bytes per row (192 keys), kMmaK = keys per MMA, kBStages = library
+// ring stages, kBParts = bulk copies per library tile.
+struct Fp8 {
+  static constexpr int kRows = 256;
+  static constexpr int kKBytes = 192;
+  static constexpr int kMmaK = 32;
+  static constexpr int kBStages = 3;
+  static constexpr int kBParts = 3;
+  static constexpr bool kFp4 = false;
+  static constexpr uint32_t kAccStride = 256;   // TMEM columns between the two accumulators
+};
+struct Fp4 {
+  static constexpr int kRows = 192;
+  static constexpr int kKBytes = 96;
+  static constexpr int kMmaK = 64;
+  static constexpr int kBStages = 6;
+  static constexpr int kBParts = 2;
+  static constexpr bool kFp4 = true;
+  static constexpr uint32_t kAccStride = 256;   // accumulators at columns 0 and 256, 192 wide
+  static constexpr uint32_t kSfaCol = 192;      // scale factors beside them (every byte 127: scale 1)
+  static constexpr uint32_t kSfbCol = 448;
+  static constexpr int kSfCols = 64;
+};
+
+template <class F>
+struct Geom {
+  static constexpr int kChunks = F::kKBytes / 16;           // 16-byte K chunks per row
+  static constexpr int kSbo = kLbo * kChunks;               // bytes between 8-row groups
+  static constexpr int kBTileBytes = F::kRows * F::kKBytes;
+  static constexpr int kATileBytes = kTcQ * F::kKBytes;
+  static constexpr int kMmas = 192 / F::kMmaK;              // MMAs per library tile
+  static constexpr int kSliceBytes = F::kMmaK * F::kKBytes / 192;   // operand bytes of one K slice per row
+  static_assert(kSliceBytes == 32, "each K slice spans two core matrices along K");
+  static_assert((kBTileBytes / F::kBParts) % 16 == 0, "bulk copies move multiples of 16 bytes");
+};
 
 // ------------------------------------------------------------------ PTX helpers
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -135,34 +170,53 @@ __device__ __forceinline__ void st_release_smem(uint32_t* p, uint32_t v) {
 }
 
 // Shared-memory matrix descriptor: K-major, no swizzle (layout type 0).
+template <class F>
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
   uint64_t d = 0;
   d |= static_cast<uint64_t>((addr >> 4) & 0x3FFFu);
   d |= static_cast<uint64_t>((kLbo >> 4) & 0x3FFFu) << 16;
-  d |= static_cast<uint64_t>((kSbo >> 4) & 0x3FFFu) << 32;
+  d |= static_cast<uint64_t>((Geom<F>::kSbo >> 4) & 0x3FFFu) << 32;
   d |= 1ull << 46;  // descriptor version for tcgen05
   return d;
 }
 
-// Instruction descriptor of kind::f8f6f4: dense, A = B = E4M3 (format 0),
-// D = F16 (format 0 at bits 4-5; every sum is an integer <= 166, exact in FP16),
-// both K-major, N = 256 (N >> 3 at bit 17), M = 128 (M >> 4 at bit 24).
+// Instruction descriptors.
+// kind::f8f6f4: dense, A = B = E4M3 (format 0 at bits 7 and 10), D = F16 (format 0 at
+// bits 4-5; every sum is an integer <= 166, exact in FP16), both K-major, N >> 3 at
+// bit 17, M >> 4 at bit 24.
+// kind::mxf4 (block-scaled): dense, scale-factor ids 0 (bits 4-5, 29-30), A = B = E2M1
+// (MXF4 format 1 at bits 7 and 10), both K-major, N >> 3 at bit 17, scale type UE8M0
+// (bit 23), M >> 4 at bit 24, K = 64 per MMA (bit 31 clear); D is FP32.
+template <class F>
 __device__ __forceinline__ uint32_t instr_desc() {
   uint32_t d = 0;
-  d |= 0u << 4;                           // D format: F16
-  d |= 0u << 7;                           // A format: E4M3
-  d |= 0u << 10;                          // B format: E4M3
-  d |= static_cast<uint32_t>(kTcRows >> 3) << 17;
+  if constexpr (F::kFp4) {
+    d |= 1u << 7;
+    d |= 1u << 10;
+    d |= 1u << 23;
+  }
+  d |= static_cast<uint32_t>(F::kRows >> 3) << 17;
   d |= static_cast<uint32_t>(kTcQ >> 4) << 24;
   return d;
 }
 
-__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc)
-      : "memory");
+template <class F>
+__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc,
+                                    uint32_t sfa, uint32_t sfb) {
+  if constexpr (F::kFp4) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::mxf4.block_scale.scale_vec::2X [%0], %1, %2, %3, [%5], [%6], p;\n}\n" ::"r"(
+            d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc), "r"(sfa), "r"(sfb)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+  }
 }
 
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
@@ -184,7 +238,31 @@ __device__ __forceinline__ void tmem_ld64h_nowait(uint32_t taddr, uint32_t (&v)[
       : "memory");
 }
 
+// 32 consecutive 32-bit TMEM columns of this thread's lane (FP32 accumulators);
+// valid only after tmem_wait_ld().
+__device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+        "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+        "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr)
+      : "memory");
+}
+
+// 32 consecutive TMEM columns of this thread's lane := w.
+__device__ __forceinline__ void tmem_st32_fill(uint32_t taddr, uint32_t w) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, "
+      "%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1};" ::"r"(taddr),
+      "r"(w)
+      : "memory");
+}
+
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ void red_add_u32(uint32_t* p, uint32_t v) {
   asm volatile("red.relaxed.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
@@ -197,12 +275,13 @@ __device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t* p) {
 }
 
 // Byte offset of (row, key byte) inside a K-major no-swizzle operand tile.
+template <class F>
 __host__ __device__ __forceinline__ uint32_t op_offset(int row, int kb) {
-  return static_cast<uint32_t>((row >> 3) * kSbo + (kb >> 4) * kLbo + (row & 7) * 16 + (kb & 15));
+  return static_cast<uint32_t>((row >> 3) * Geom<F>::kSbo + (kb >> 4) * kLbo + (row & 7) * 16 + (kb & 15));
 }
 
-// 16 operand bytes of one record: keys 16c .. 16c+15 as 0 / one.
-__device__ __forceinline__ uint4 operand_chunk(uint64_t w0, uint64_t w1, uint64_t w2, int c, uint32_t one) {
+// 16 FP8 operand bytes of one record: keys 16c .. 16c+15 as 0 / one (0x38).
+__device__ __forceinline__ uint4 operand_chunk8(uint64_t w0, uint64_t w1, uint64_t w2, int c) {
   uint32_t out[4];
 #pragma unroll
   for (int b = 0; b < 4; ++b) {
@@ -212,46 +291,81 @@ __device__ __forceinline__ uint4 operand_chunk(uint64_t w0, uint64_t w1, uint64_
       int j = 16 * c + 4 * b + e;
       uint64_t w = j < 64 ? w0 : (j < 128 ? w1 : w2);
       uint32_t bit = (j < kBits) ? static_cast<uint32_t>((w >> (j & 63)) & 1ull) : 0u;
-      v |= (bit ? one : 0u) << (8 * e);
+      v |= (bit ? 0x38u : 0u) << (8 * e);
     }
     out[b] = v;
   }
   return make_uint4(out[0], out[1], out[2], out[3]);
 }
 
+// 16 FP4 operand bytes of one record: keys 32c .. 32c+31, two per byte (key 32c + 2j in
+// the low nibble of byte j, key 32c + 2j + 1 in its high nibble), E2M1 0 or one (0x2).
+// Keys past 165 are zero bits of the packed record.
+__device__ __forceinline__ uint4 operand_chunk4(uint64_t w0, uint64_t w1, uint64_t w2, int c) {
+  const uint64_t w = c < 2 ? w0 : (c < 4 ? w1 : w2);
+  const uint32_t bits = static_cast<uint32_t>(w >> (32 * (c & 1)));
+  uint32_t out[4];
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    uint32_t v = 0;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v |= ((bits >> (8 * b + e)) & 1u) << (4 * e + 1);
+    out[b] = v;
+  }
+  return make_uint4(out[0], out[1], out[2], out[3]);
+}
+
+template <class F>
+__device__ __forceinline__ uint4 operand_chunk(uint64_t w0, uint64_t w1, uint64_t w2, int c) {
+  if constexpr (F::kFp4)
+    return operand_chunk4(w0, w1, w2, c);
+  else
+    return operand_chunk8(w0, w1, w2, c);
+}
+
 // ------------------------------------------------------------- operand build
-// Library operand: tensor tile T covers scan tiles 2T and 2T+1 (records 256T ..).
-__global__ void tc_pack_library_kernel(DevLib lib, uint8_t* op, int64_t n_tc, uint32_t one) {
-  const int64_t total = n_tc * kTcRows * (kKBytes / 16);
+// Library operand: tensor tile T holds layout positions T * kRows .. + kRows - 1;
+// positions past the layout (the last FP4 tile) are zero rows.
+template <class F>
+__global__ void tc_pack_library_kernel(DevLib lib, uint8_t* op, int64_t n_tc) {
+  constexpr int kC = Geom<F>::kChunks;
+  const int64_t n_pos = lib.n_tiles * kTile;
+  const int64_t total = n_tc * F::kRows * kC;
   for (int64_t u = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; u < total;
        u += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    int64_t T = u / (kTcRows * 12);
-    int rem = static_cast<int>(u % (kTcRows * 12));
-    int g = rem / 96, rr = (rem % 96) % 8, c = (rem % 96) / 8;
-    int row = 8 * g + rr;
-    int64_t pos = T * kTcRows + row;
-    const uint64_t* w = lib.words + (pos / kTile) * (kWords * kTile) + (pos % kTile);
-    uint4 v = operand_chunk(w[0], w[kTile], w[2 * kTile], c, one);
-    *reinterpret_cast<uint4*>(op + T * kBTileBytes + op_offset(row, 16 * c)) = v;
+    const int64_t T = u / (F::kRows * kC);
+    const int rem = static_cast<int>(u % (F::kRows * kC));
+    const int g = rem / (8 * kC), rr = (rem % (8 * kC)) % 8, c = (rem % (8 * kC)) / 8;
+    const int row = 8 * g + rr;
+    const int64_t pos = T * F::kRows + row;
+    uint4 v = make_uint4(0, 0, 0, 0);
+    if (pos < n_pos) {
+      const uint64_t* w = lib.words + (pos / kTile) * (kWords * kTile) + (pos % kTile);
+      v = operand_chunk<F>(w[0], w[kTile], w[2 * kTile], c);
+    }
+    *reinterpret_cast<uint4*>(op + T * Geom<F>::kBTileBytes + op_offset<F>(row, 16 * c)) = v;
   }
 }
 
 // Query operand: Q rounded up to 128-row tiles, rows past Q are zero.
-__global__ void tc_pack_queries_kernel(const uint64_t* q, int Q, uint8_t* op, int q_tiles, uint32_t one) {
-  const int total = q_tiles * kTcQ * 12;
+template <class F>
+__global__ void tc_pack_queries_kernel(const uint64_t* q, int Q, uint8_t* op, int q_tiles) {
+  constexpr int kC = Geom<F>::kChunks;
+  const int total = q_tiles * kTcQ * kC;
   for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < total; u += gridDim.x * blockDim.x) {
-    int t = u / (kTcQ * 12), rem = u % (kTcQ * 12);
-    int g = rem / 96, rr = (rem % 96) % 8, c = (rem % 96) / 8;
-    int row = 8 * g + rr, qi = t * kTcQ + row;
+    const int t = u / (kTcQ * kC), rem = u % (kTcQ * kC);
+    const int g = rem / (8 * kC), rr = (rem % (8 * kC)) % 8, c = (rem % (8 * kC)) / 8;
+    const int row = 8 * g + rr, qi = t * kTcQ + row;
     uint4 v = make_uint4(0, 0, 0, 0);
-    if (qi < Q) v = operand_chunk(q[3 * qi], q[3 * qi + 1], q[3 * qi + 2], c, one);
-    *reinterpret_cast<uint4*>(op + static_cast<size_t>(t) * kATileBytes + op_offset(row, 16 * c)) = v;
+    if (qi < Q) v = operand_chunk<F>(q[3 * qi], q[3 * qi + 1], q[3 * qi + 2], c);
+    *reinterpret_cast<uint4*>(op + static_cast<size_t>(t) * Geom<F>::kATileBytes + op_offset<F>(row, 16 * c)) = v;
   }
 }
 
 // ------------------------------------------------------------------- scan
-// One epilogue lane's 64 FP16 accumulators (a query against 64 records) that
-// passed the tile-level test, with what the flusher needs to finish the compare:
+// One epilogue lane's group of up to 64 accumulators (a query against up to 64
+// records) that passed the group-level test, as FP16, with what the flusher needs to
+// finish the compare:
 //   m0 = need (FP16 bit pattern) | valid columns << 16,
 //   m1 = popc q + popc x | item sequence << 9,  pos0 = layout position of column 0,
 //   coff, cap = the query's candidate region (first key, keys);
@@ -264,16 +378,17 @@ struct RingEntry {
 };
 static_assert(sizeof(RingEntry) == 160, "ring entry layout");
 
+template <class F>
 struct TcSmem {
-  uint8_t a[2][kATileBytes];
-  uint8_t b[kBStages][kBTileBytes];
-  uint64_t b_full[kBStages], b_empty[kBStages];
+  uint8_t a[2][Geom<F>::kATileBytes];
+  uint8_t b[F::kBStages][Geom<F>::kBTileBytes];
+  uint64_t b_full[F::kBStages], b_empty[F::kBStages];
   uint64_t a_full[2], a_empty[2];
   uint64_t acc_full[2], acc_empty[2];
   uint64_t fin;
   uint32_t tmem_base;
-  int tile_off2[kNumBuckets + 1];  // first tensor tile of each bucket
-  int bcount[kNumBuckets + 1];
+  int bpos[kNumBuckets + 1];       // first layout position of each bucket
+  int bend[kNumBuckets + 1];       // one past its last record
   RingEntry ring[kRingCap];
   // per query row: (item sequence << 32) | ~bound -- a 64-bit max keeps the newest
   // item and, within it, the smallest bound
@@ -287,33 +402,35 @@ struct TcSmem {
   uint32_t ref_head[kFlushWarps];  // refresh requests done (refresher)
   uint32_t flush_done;             // flushers finished
 };
-static_assert(sizeof(TcSmem) + 1024 <= 232448, "shared memory per CTA");
+static_assert(sizeof(TcSmem<Fp8>) + 1024 <= 232448, "shared memory per CTA");
+static_assert(sizeof(TcSmem<Fp4>) + 1024 <= 232448, "shared memory per CTA");
 
 // Every ring slot below this one is retired.  A flusher never passes a slot that
 // is claimed and unwritten, so the minimum of the heads is at most any such slot.
-__device__ __forceinline__ uint32_t ring_retired(const TcSmem& S) {
-  uint32_t m = ld_acquire_smem(&S.f_head[0]);
+template <class S>
+__device__ __forceinline__ uint32_t ring_retired(const S& sm) {
+  uint32_t m = ld_acquire_smem(&sm.f_head[0]);
 #pragma unroll
-  for (int f = 1; f < kFlushWarps; ++f) m = min(m, ld_acquire_smem(&S.f_head[f]));
+  for (int f = 1; f < kFlushWarps; ++f) m = min(m, ld_acquire_smem(&sm.f_head[f]));
   return m;
 }
 
-// Epilogue side: claim a ring slot, wait (bounded) for room, write the entry.
-__device__ __forceinline__ bool ring_push(TcSmem& S, const uint32_t (&w)[32], uint32_t q, uint32_t m0, uint32_t m1,
-                                          uint32_t pos0, unsigned long long coff, uint32_t cap,
-                                          uint64_t timeout_ns) {
-  const uint32_t slot = atomicAdd(&S.r_tail, 1u);
-  if (slot - ring_retired(S) >= kRingCap) {
+// Epilogue side: claim a ring slot, wait (bounded) for room, write the entry
+// (fill(e) writes its 64 FP16 values).
+template <class S, class Fill>
+__device__ __forceinline__ bool ring_push(S& sm, Fill&& fill, uint32_t q, uint32_t m0, uint32_t m1, uint32_t pos0,
+                                          unsigned long long coff, uint32_t cap, uint64_t timeout_ns) {
+  const uint32_t slot = atomicAdd(&sm.r_tail, 1u);
+  if (slot - ring_retired(sm) >= kRingCap) {
     // the ring is full: wait without taking issue slots from the flushers
     const uint64_t deadline = global_ns() + timeout_ns;
-    while (slot - ring_retired(S) >= kRingCap) {
+    while (slot - ring_retired(sm) >= kRingCap) {
       if (global_ns() > deadline) return false;
       __nanosleep(64);
     }
   }
-  RingEntry& e = S.ring[slot % kRingCap];
-#pragma unroll
-  for (int i = 0; i < 8; ++i) e.v[i] = make_uint4(w[4 * i], w[4 * i + 1], w[4 * i + 2], w[4 * i + 3]);
+  RingEntry& e = sm.ring[slot % kRingCap];
+  fill(e);
   *reinterpret_cast<uint4*>(&e.q) = make_uint4(q, m0, m1, pos0);
   e.cap = cap;
   e.coff = coff;
@@ -336,12 +453,13 @@ __device__ __forceinline__ int nth_set_bit(uint32_t m, uint32_t r) {
   return pos;
 }
 
-// Bucket of tensor tile T (tiles of one bucket are contiguous).
-__device__ __forceinline__ int bucket_of(const int* off2, int64_t T) {
+// Bucket of layout position p: the last bucket starting at or before p (empty
+// buckets start where the next one does).
+__device__ __forceinline__ int bucket_at(const int* bpos, int64_t p) {
   int lo = 0, hi = kNumBuckets - 1;
   while (lo < hi) {
     int mid = (lo + hi + 1) >> 1;
-    if (off2[mid] <= T)
+    if (bpos[mid] <= p)
       lo = mid;
     else
       hi = mid - 1;
@@ -349,21 +467,38 @@ __device__ __forceinline__ int bucket_of(const int* off2, int64_t T) {
   return lo;
 }
 
+// FP32 accumulators of a group that passed, as FP16 pairs (column 2i low, 2i + 1 high);
+// every value is an integer <= 166, exact in FP16.
+__device__ __forceinline__ uint32_t half2_bits(uint32_t lo, uint32_t hi) {
+  const __half2 h = __floats2half2_rn(__uint_as_float(lo), __uint_as_float(hi));
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+// Largest of 32 non-negative FP32 bit patterns (they order like unsigned integers).
+__device__ __forceinline__ uint32_t max32_u32(const uint32_t (&v)[32]) {
+  uint32_t m = __vimax3_u32(v[0], v[1], v[2]);
+#pragma unroll
+  for (int e = 3; e < 31; e += 2) m = __vimax3_u32(m, v[e], v[e + 1]);
+  return max(m, v[31]);
+}
+
+template <class F>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_scan_kernel(DevLib lib, BatchDev b, const uint8_t* __restrict__ lib_op, const uint8_t* __restrict__ q_op,
-                   int64_t n_tc, int n_qt, uint64_t timeout_ns) {
+                   int64_t n_tc, int n_qt, int chunk, uint64_t timeout_ns) {
+  using G = Geom<F>;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
-  TcSmem& S = *reinterpret_cast<TcSmem*>(smem_raw);
+  TcSmem<F>& S = *reinterpret_cast<TcSmem<F>*>(smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t n_chunks = (n_tc + kChunkTiles - 1) / kChunkTiles;
+  const int64_t n_chunks = (n_tc + chunk - 1) / chunk;
   const int64_t n_items = n_chunks * n_qt;
 
   for (int i = threadIdx.x; i < kNumBuckets + 1; i += blockDim.x) {
-    S.tile_off2[i] = lib.tile_off[i] / 2;
-    S.bcount[i] = i < kNumBuckets ? lib.bcount[i] : 0;
+    S.bpos[i] = lib.tile_off[i] * kTile;
+    S.bend[i] = i < kNumBuckets ? lib.tile_off[i] * kTile + lib.bcount[i] : S.bpos[i];
   }
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kBStages; ++s) {
+    for (int s = 0; s < F::kBStages; ++s) {
       mbar_init(&S.b_full[s], 1);
       mbar_init(&S.b_empty[s], 1);
     }
@@ -399,6 +534,21 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = S.tmem_base;
+  if constexpr (F::kFp4) {
+    // unit scale factors: every byte of both scale-factor regions is 127 (2^0) in every lane
+    if (warp >= 2 && warp < 6) {
+      const uint32_t lane_base = tmem + (static_cast<uint32_t>(32 * (warp & 3)) << 16);
+#pragma unroll
+      for (int c = 0; c < F::kSfCols; c += 32) {
+        tmem_st32_fill(lane_base + F::kSfaCol + c, 0x7F7F7F7Fu);
+        tmem_st32_fill(lane_base + F::kSfbCol + c, 0x7F7F7F7Fu);
+      }
+      tmem_wait_st();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+  }
   const uint64_t deadline = timeout_ns;   // per wait
   const uint64_t drain = timeout_ns > kDrainNs ? timeout_ns : kDrainNs;   // own copies / MMAs in flight
   bool ok = true;
@@ -418,28 +568,29 @@ __global__ void __launch_bounds__(kThreads, 1)
           ok = false;
           break;
         }
-        mbar_arrive_expect_tx(&S.a_full[ab], kATileBytes);
-        bulk_g2s(S.a[ab], q_op + static_cast<size_t>(qt) * kATileBytes, kATileBytes, &S.a_full[ab]);
+        mbar_arrive_expect_tx(&S.a_full[ab], G::kATileBytes);
+        bulk_g2s(S.a[ab], q_op + static_cast<size_t>(qt) * G::kATileBytes, G::kATileBytes, &S.a_full[ab]);
         ++na;
-        const int64_t t0 = c * kChunkTiles, t1 = min(t0 + kChunkTiles, n_tc);
+        const int64_t t0 = c * chunk, t1 = min(t0 + chunk, n_tc);
         for (int64_t T = t0; T < t1; ++T, ++bn) {
-          const int s = static_cast<int>(bn % kBStages);
-          const uint32_t use = bn / kBStages;
+          const int s = static_cast<int>(bn % F::kBStages);
+          const uint32_t use = bn / F::kBStages;
           if (!mbar_wait(&S.b_empty[s], (use & 1) ^ 1, deadline)) {
             ok = false;
             break;
           }
-          mbar_arrive_expect_tx(&S.b_full[s], kBTileBytes);
-          const uint8_t* src = lib_op + T * kBTileBytes;
+          mbar_arrive_expect_tx(&S.b_full[s], G::kBTileBytes);
+          const uint8_t* src = lib_op + T * G::kBTileBytes;
+          constexpr int kPart = G::kBTileBytes / F::kBParts;
 #pragma unroll
-          for (int part = 0; part < 3; ++part)
-            bulk_g2s(S.b[s] + part * (kBTileBytes / 3), src + part * (kBTileBytes / 3), kBTileBytes / 3, &S.b_full[s]);
+          for (int part = 0; part < F::kBParts; ++part)
+            bulk_g2s(S.b[s] + part * kPart, src + part * kPart, kPart, &S.b_full[s]);
         }
       }
       // wait (bounded) for copies still in flight before anyone leaves
-      for (int s = 0; s < kBStages; ++s) {
+      for (int s = 0; s < F::kBStages; ++s) {
         if (bn > static_cast<uint32_t>(s)) {
-          uint32_t last_use = (bn - 1 - s) / kBStages;
+          uint32_t last_use = (bn - 1 - s) / F::kBStages;
           mbar_wait(&S.b_full[s], last_use & 1, drain);
         }
       }
@@ -454,7 +605,12 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issue
     if (lane == 0) {
-      const uint32_t idesc = instr_desc();
+      const uint32_t idesc = instr_desc<F>();
+      uint32_t sfa = 0, sfb = 0;
+      if constexpr (F::kFp4) {
+        sfa = tmem + F::kSfaCol;
+        sfb = tmem + F::kSfbCol;
+      }
       uint32_t bn = 0, tn = 0;  // library tiles consumed, accumulators produced
       for (int64_t j = 0; ok; ++j) {
         const int64_t item = blockIdx.x + j * gridDim.x;
@@ -467,21 +623,22 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         tc_fence_after();
         const uint32_t a_base = smem_addr(S.a[ab]);
-        const int64_t t0 = c * kChunkTiles, t1 = min(t0 + kChunkTiles, n_tc);
+        const int64_t t0 = c * chunk, t1 = min(t0 + chunk, n_tc);
         for (int64_t T = t0; T < t1; ++T, ++bn, ++tn) {
-          const int s = static_cast<int>(bn % kBStages);
+          const int s = static_cast<int>(bn % F::kBStages);
           const int acc = static_cast<int>(tn & 1);
           if (!mbar_wait(&S.acc_empty[acc], ((tn >> 1) & 1) ^ 1, deadline) ||
-              !mbar_wait(&S.b_full[s], (bn / kBStages) & 1, deadline)) {
+              !mbar_wait(&S.b_full[s], (bn / F::kBStages) & 1, deadline)) {
             ok = false;
             break;
           }
           tc_fence_after();
           const uint32_t b_base = smem_addr(S.b[s]);
-          const uint32_t d_tmem = tmem + static_cast<uint32_t>(acc * kTcRows);
+          const uint32_t d_tmem = tmem + static_cast<uint32_t>(acc) * F::kAccStride;
 #pragma unroll
-          for (int ks = 0; ks < kKBytes / 32; ++ks)
-            mma(d_tmem, smem_desc(a_base + 256 * ks), smem_desc(b_base + 256 * ks), idesc, ks > 0 ? 1u : 0u);
+          for (int ks = 0; ks < G::kMmas; ++ks)
+            mma<F>(d_tmem, smem_desc<F>(a_base + 256 * ks), smem_desc<F>(b_base + 256 * ks), idesc,
+                   ks > 0 ? 1u : 0u, sfa, sfb);
           mma_commit(&S.b_empty[s]);
           mma_commit(&S.acc_full[acc]);
         }
@@ -497,11 +654,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     // -------------------------------------------------------------- epilogue
     const int ew = warp - 2;
     const int quarter = warp & 3;                 // TMEM lanes 32*quarter .. +31
-    const int half = ew >> 2;                     // columns 128*half .. +127
+    const int half = ew >> 2;                     // which half of the tile's columns
     const int row = 32 * quarter + lane;          // query row inside the tile
     const uint32_t lane_addr = static_cast<uint32_t>(32 * quarter) << 16;
     uint32_t tn = 0;
-    int bk = 0;                                   // bucket cursor (tiles arrive in ascending order per item)
+    int bk = 0;                                   // bucket cursor (positions ascend within an item)
     for (int64_t j = 0; ok; ++j) {
       const int64_t item = blockIdx.x + j * gridDim.x;
       if (item >= n_items) break;
@@ -510,22 +667,19 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int q = qt * kTcQ + row;
       const bool live = q < b.Q && b.k[q] > 0;
       int pq = 0;
-      uint32_t thr = 0, ccap = 0;
-      unsigned long long coff = 0;
-      const unsigned long long jkey = static_cast<unsigned long long>(j) << 32;
+      uint32_t thr = 0;
       if (live) {
         pq = __popcll(b.queries[3 * q]) + __popcll(b.queries[3 * q + 1]) + __popcll(b.queries[3 * q + 2]);
-        coff = static_cast<unsigned long long>(b.cand_off[q]);
-        ccap = static_cast<uint32_t>(b.cand_off[q + 1] - b.cand_off[q]);
         thr = ld_relaxed_u32(b.thr + q);
-        atomicMax(&S.thr_w[row], jkey | (0xFFFFFFFFu - thr));
+        atomicMax(&S.thr_w[row], (static_cast<unsigned long long>(j) << 32) | (0xFFFFFFFFu - thr));
       }
-      const int64_t t0 = c * kChunkTiles, t1 = min(t0 + kChunkTiles, n_tc);
-      bk = bucket_of(S.tile_off2, t0);
+      // tile indices and layout positions fit 32 bits (positions index the int32 perm)
+      const int t0 = static_cast<int>(c * chunk), t1 = static_cast<int>(min(c * chunk + chunk, n_tc));
+      bk = bucket_at(S.bpos, static_cast<int64_t>(t0) * F::kRows);
       // other CTAs' refreshes of this query reach the row through the global
       // bound, re-read every 8 tiles (loaded one tile before it is used)
       uint32_t gthr = thr;
-      for (int64_t T = t0; T < t1; ++T, ++tn) {
+      for (int T = t0; T < t1; ++T, ++tn) {
         const int acc = static_cast<int>(tn & 1);
         if (live) {   // the refresher may have tightened this row's bound
           const unsigned long long w = *reinterpret_cast<volatile unsigned long long*>(&S.thr_w[row]);
@@ -536,53 +690,136 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (((T - t0) & 7) == 1) thr = gthr < thr ? gthr : thr;
           if (((T - t0) & 7) == 0) gthr = ld_relaxed_u32(b.thr + q);
         }
-        while (bk + 1 < kNumBuckets && S.tile_off2[bk + 1] <= T) ++bk;
-        int nvalid = S.bcount[bk] - static_cast<int>(T - S.tile_off2[bk]) * kTcRows;
-        nvalid = nvalid < kTcRows ? nvalid : kTcRows;
-        const bool act = live && static_cast<uint32_t>(abs(bk - pq)) <= thr;
-        // acc >= (pq + px - thr) / 2  <=>  d <= thr;  twice the bar keeps it an integer
-        const int bar2 = pq + bk - static_cast<int>(thr);
-        const bool landed = mbar_wait(&S.acc_full[acc], (tn >> 1) & 1, deadline);
-        if (!__all_sync(kFull, landed)) {   // one verdict for the whole warp
-          ok = false;
-          break;
-        }
-        tc_fence_after();
-        uint32_t v[2][32];
-        const bool any_act = __any_sync(kFull, act);
-        if (any_act) {
-          const uint32_t col0 = static_cast<uint32_t>(acc * kTcRows + half * 128);
-          tmem_ld64h_nowait(tmem + lane_addr + col0, v[0]);
-          tmem_ld64h_nowait(tmem + lane_addr + col0 + 64, v[1]);
-          tmem_wait_ld();
-        }
-        // the values are in registers: hand the accumulator back to the MMA before comparing
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&S.acc_empty[acc]);
-        if (act) {
-          // acc >= ceil(bar2 / 2); non-negative FP16 bit patterns order like unsigned ints
-          const int need = (bar2 + 1) >> 1;
-          const uint32_t need16 = need <= 0 ? 0u : static_cast<uint32_t>(__half_as_ushort(__int2half_rn(need)));
-          auto group = [&](const uint32_t (&w)[32], int g) {
-            uint32_t m = __vimax3_u16x2(w[0], w[1], w[2]);
+        const int tpos = T * F::kRows;            // layout position of the tile's column 0
+        // a group of columns passes when acc >= ceil((pq + px - thr) / 2) for one of its
+        // records: the largest accumulator against the bar of the group's bucket px
+        auto bar_of = [&](int px, uint32_t& need16) {
+          const int need = (pq + px - static_cast<int>(thr) + 1) >> 1;
+          need16 = need <= 0 ? 0u : static_cast<uint32_t>(__half_as_ushort(__int2half_rn(need)));
+          return need <= 0 ? 0u : __float_as_uint(static_cast<float>(need));
+        };
+        auto push = [&](auto&& fill, uint32_t need16, int px, int p0, int ncols) {
+          int lim = S.bend[px] - p0;
+          lim = lim < ncols ? lim : ncols;
+          if (lim <= 0) return;
+          // the query's candidate region (read here: passing groups are rare)
+          const int64_t co = b.cand_off[q];
+          const uint32_t ccap = static_cast<uint32_t>(b.cand_off[q + 1] - co);
+          if (!ring_push(S, fill, static_cast<uint32_t>(q), need16 | (static_cast<uint32_t>(lim) << 16),
+                         static_cast<uint32_t>(pq + px) | (static_cast<uint32_t>(j) << 9), static_cast<uint32_t>(p0),
+                         static_cast<unsigned long long>(co), ccap, deadline))
+            ok = false;
+        };
+        if constexpr (!F::kFp4) {
+          // FP8: a 256-record tile lies inside one bucket; this warp reads columns
+          // 128 half .. +127 as two groups of 64 FP16 values (pack::16b)
+          while (bk + 1 < kNumBuckets && S.bpos[bk + 1] <= tpos) ++bk;
+          const bool act = live && static_cast<uint32_t>(abs(bk - pq)) <= thr;
+          const bool landed = mbar_wait(&S.acc_full[acc], (tn >> 1) & 1, deadline);
+          if (!__all_sync(kFull, landed)) {   // one verdict for the whole warp
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          uint32_t v[2][32];
+          if (__any_sync(kFull, act)) {
+            const uint32_t col0 = static_cast<uint32_t>(acc) * F::kAccStride + static_cast<uint32_t>(half * 128);
+            tmem_ld64h_nowait(tmem + lane_addr + col0, v[0]);
+            tmem_ld64h_nowait(tmem + lane_addr + col0 + 64, v[1]);
+            tmem_wait_ld();
+          }
+          // the values are in registers: hand the accumulator back to the MMA before comparing
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&S.acc_empty[acc]);
+          if (act) {
+            uint32_t need16;
+            bar_of(bk, need16);
 #pragma unroll
-            for (int e = 3; e < 31; e += 2) m = __vimax3_u16x2(m, w[e], w[e + 1]);
-            m = __vmaxu2(m, w[31]);
-            if (max(m & 0xFFFFu, m >> 16) < need16) return;
-            // rare: some of these 64 records may be within the bound; the flusher
-            // finishes the compare column by column
-            const int colb = half * 128 + g * 64;
-            int lim = nvalid - colb;
-            lim = lim < 64 ? lim : 64;
-            if (lim <= 0) return;
-            if (!ring_push(S, w, static_cast<uint32_t>(q), need16 | (static_cast<uint32_t>(lim) << 16),
-                           static_cast<uint32_t>(pq + bk) | (static_cast<uint32_t>(j) << 9),
-                           static_cast<uint32_t>(T * kTcRows + colb), coff, ccap, deadline))
-              ok = false;
-          };
-          group(v[0], 0);
-          group(v[1], 1);
+            for (int g = 0; g < 2; ++g) {
+              uint32_t m = __vimax3_u16x2(v[g][0], v[g][1], v[g][2]);
+#pragma unroll
+              for (int e = 3; e < 31; e += 2) m = __vimax3_u16x2(m, v[g][e], v[g][e + 1]);
+              m = __vmaxu2(m, v[g][31]);
+              // rare: some of these 64 records may be within the bound; the flusher
+              // finishes the compare column by column
+              if (max(m & 0xFFFFu, m >> 16) >= need16) {
+                auto fill = [&](RingEntry& e) {
+#pragma unroll
+                  for (int i = 0; i < 8; ++i)
+                    e.v[i] = make_uint4(v[g][4 * i], v[g][4 * i + 1], v[g][4 * i + 2], v[g][4 * i + 3]);
+                };
+                push(fill, need16, bk, tpos + half * 128 + g * 64, 64);
+              }
+            }
+          }
+        } else {
+          // FP4: a 192-record tile may span two buckets (boundaries fall on multiples of 64
+          // columns); this warp reads group A = columns 64 half .. +63 and group B =
+          // columns 128 + 32 half .. +31, each inside one bucket, as FP32 values
+          const int pA = tpos + 64 * half, pB = tpos + 128 + 32 * half;
+          while (bk + 1 < kNumBuckets && S.bpos[bk + 1] <= pA) ++bk;
+          const int bkA = bk;
+          while (bk + 1 < kNumBuckets && S.bpos[bk + 1] <= pB) ++bk;
+          const int bkB = bk;
+          const bool actA = live && static_cast<uint32_t>(abs(bkA - pq)) <= thr;
+          const bool actB = live && static_cast<uint32_t>(abs(bkB - pq)) <= thr;
+          const bool landed = mbar_wait(&S.acc_full[acc], (tn >> 1) & 1, deadline);
+          if (!__all_sync(kFull, landed)) {   // one verdict for the whole warp
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          // group A (64 columns) is read and tested first, then group B (32 columns): two
+          // waits, so that at most 64 accumulators are in registers at a time.  A passing
+          // group (rare) goes to the ring before the accumulator is released: keeping its
+          // FP16 pairs across the release does not fit the register budget
+          uint32_t needA16 = 0, needB16 = 0;
+          const uint32_t needA = bar_of(bkA, needA16), needB = bar_of(bkB, needB16);
+          if (__any_sync(kFull, actA || actB)) {
+            const uint32_t base = tmem + lane_addr + static_cast<uint32_t>(acc) * F::kAccStride;
+            {
+              uint32_t v0[32], v1[32];
+              tmem_ld32_nowait(base + 64 * half, v0);
+              tmem_ld32_nowait(base + 64 * half + 32, v1);
+              tmem_wait_ld();
+              if (actA && max(max32_u32(v0), max32_u32(v1)) >= needA) {
+                auto fill = [&](RingEntry& e) {
+#pragma unroll
+                  for (int i = 0; i < 4; ++i) {
+                    e.v[i] = make_uint4(half2_bits(v0[8 * i], v0[8 * i + 1]), half2_bits(v0[8 * i + 2], v0[8 * i + 3]),
+                                        half2_bits(v0[8 * i + 4], v0[8 * i + 5]),
+                                        half2_bits(v0[8 * i + 6], v0[8 * i + 7]));
+                    e.v[4 + i] = make_uint4(half2_bits(v1[8 * i], v1[8 * i + 1]),
+                                            half2_bits(v1[8 * i + 2], v1[8 * i + 3]),
+                                            half2_bits(v1[8 * i + 4], v1[8 * i + 5]),
+                                            half2_bits(v1[8 * i + 6], v1[8 * i + 7]));
+                  }
+                };
+                push(fill, needA16, bkA, pA, 64);
+              }
+            }
+            {
+              uint32_t v2[32];
+              tmem_ld32_nowait(base + 128 + 32 * half, v2);
+              tmem_wait_ld();
+              if (actB && max32_u32(v2) >= needB) {
+                auto fill = [&](RingEntry& e) {
+#pragma unroll
+                  for (int i = 0; i < 4; ++i) {
+                    e.v[i] = make_uint4(half2_bits(v2[8 * i], v2[8 * i + 1]), half2_bits(v2[8 * i + 2], v2[8 * i + 3]),
+                                        half2_bits(v2[8 * i + 4], v2[8 * i + 5]),
+                                        half2_bits(v2[8 * i + 6], v2[8 * i + 7]));
+                    e.v[4 + i] = make_uint4(0u, 0u, 0u, 0u);
+                  }
+                };
+                push(fill, needB16, bkB, pB, 32);
+              }
+            }
+          }
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&S.acc_empty[acc]);
         }
       }
       if (!ok) break;
@@ -830,43 +1067,79 @@ __global__ void __launch_bounds__(kThreads, 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
 }
 
-cudaError_t launch_tc(const DevLib& lib, const BatchDev& b, const uint8_t* lib_op, const uint8_t* q_op, int64_t n_tc,
-                      int n_qt, int num_sms, double timeout_s, cudaStream_t s) {
-  const size_t smem = sizeof(TcSmem) + 1024;
+
+template <class F>
+int64_t tensor_tiles(int64_t n_tiles128) {
+  return (n_tiles128 * kTile + F::kRows - 1) / F::kRows;
+}
+
+template <class F>
+cudaError_t launch_tc(const DevLib& lib, const BatchDev& b, const uint8_t* lib_op, const uint8_t* q_op, int n_qt,
+                      int num_sms, int chunk, double timeout_s, cudaStream_t s) {
+  const int64_t n_tc = tensor_tiles<F>(lib.n_tiles);
+  if (n_tc == 0 || n_qt == 0) return cudaSuccess;
+  const size_t smem = sizeof(TcSmem<F>) + 1024;
   static std::atomic<uint64_t> configured{0};
-  cudaError_t e = smem_attr_once(tc_scan_kernel, smem, &configured);
+  cudaError_t e = smem_attr_once(tc_scan_kernel<F>, smem, &configured);
   if (e != cudaSuccess) return e;
   const uint64_t tns = static_cast<uint64_t>((timeout_s > 0 ? timeout_s : 2.0) * 1e9);
-  tc_scan_kernel<<<num_sms, kThreads, smem, s>>>(lib, b, lib_op, q_op, n_tc, n_qt, tns);
+  tc_scan_kernel<F><<<num_sms, kThreads, smem, s>>>(lib, b, lib_op, q_op, n_tc, n_qt, chunk, tns);
+  return cudaGetLastError();
+}
+
+template <class F>
+cudaError_t pack_library(const DevLib& lib, uint8_t* op, cudaStream_t s) {
+  const int64_t n_tc = tensor_tiles<F>(lib.n_tiles);
+  if (n_tc == 0) return cudaSuccess;
+  tc_pack_library_kernel<F><<<4096, 256, 0, s>>>(lib, op, n_tc);
+  return cudaGetLastError();
+}
+
+template <class F>
+cudaError_t pack_queries(const uint64_t* q, int Q, uint8_t* op, cudaStream_t s) {
+  const int q_tiles = (Q + kTcQ - 1) / kTcQ;
+  if (q_tiles == 0) return cudaSuccess;
+  const int total = q_tiles * kTcQ * Geom<F>::kChunks;
+  tc_pack_queries_kernel<F><<<(total + 255) / 256, 256, 0, s>>>(q, Q, op, q_tiles);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-size_t tc_operand_bytes(int64_t n_tiles128) { return static_cast<size_t>((n_tiles128 + 1) / 2) * kBTileBytes; }
-size_t tc_query_operand_bytes(int Q) { return static_cast<size_t>((Q + kTcQ - 1) / kTcQ) * kATileBytes; }
-
-cudaError_t tc_pack_library(const DevLib& lib, uint8_t* op, cudaStream_t s) {
-  const int64_t n_tc = (lib.n_tiles + 1) / 2;
-  if (n_tc == 0) return cudaSuccess;
-  tc_pack_library_kernel<<<4096, 256, 0, s>>>(lib, op, n_tc, 0x38u);
-  return cudaGetLastError();
+int64_t tc_tiles(int fmt, int64_t n_tiles128) {
+  return fmt == kTcFp4 ? tensor_tiles<Fp4>(n_tiles128) : tensor_tiles<Fp8>(n_tiles128);
 }
 
-cudaError_t tc_pack_queries(const uint64_t* q, int Q, uint8_t* op, cudaStream_t s) {
-  const int q_tiles = (Q + kTcQ - 1) / kTcQ;
-  if (q_tiles == 0) return cudaSuccess;
-  const int total = q_tiles * kTcQ * 12;
-  tc_pack_queries_kernel<<<(total + 255) / 256, 256, 0, s>>>(q, Q, op, q_tiles, 0x38u);
-  return cudaGetLastError();
+int tc_tile_rows(int fmt) { return fmt == kTcFp4 ? Fp4::kRows : Fp8::kRows; }
+
+size_t tc_operand_bytes(int fmt, int64_t n_tiles128) {
+  return fmt == kTcFp4 ? static_cast<size_t>(tensor_tiles<Fp4>(n_tiles128)) * Geom<Fp4>::kBTileBytes
+                       : static_cast<size_t>(tensor_tiles<Fp8>(n_tiles128)) * Geom<Fp8>::kBTileBytes;
 }
 
-cudaError_t tc_scan(const DevLib& lib, const BatchDev& b, const uint8_t* lib_op, const uint8_t* q_op, int num_sms,
-                    double timeout_s, cudaStream_t s) {
-  const int64_t n_tc = (lib.n_tiles + 1) / 2;
+size_t tc_query_operand_bytes(int fmt, int Q) {
+  const size_t tiles = static_cast<size_t>((Q + kTcQ - 1) / kTcQ);
+  return tiles * (fmt == kTcFp4 ? Geom<Fp4>::kATileBytes : Geom<Fp8>::kATileBytes);
+}
+
+cudaError_t tc_pack_library(int fmt, const DevLib& lib, uint8_t* op, cudaStream_t s) {
+  return fmt == kTcFp4 ? pack_library<Fp4>(lib, op, s) : pack_library<Fp8>(lib, op, s);
+}
+
+cudaError_t tc_pack_queries(int fmt, const uint64_t* q, int Q, uint8_t* op, cudaStream_t s) {
+  return fmt == kTcFp4 ? pack_queries<Fp4>(q, Q, op, s) : pack_queries<Fp8>(q, Q, op, s);
+}
+
+cudaError_t tc_scan(int fmt, const DevLib& lib, const BatchDev& b, const uint8_t* lib_op, const uint8_t* q_op,
+                    int num_sms, int chunk, double timeout_s, cudaStream_t s) {
   const int n_qt = (b.Q + kTcQ - 1) / kTcQ;
-  if (n_tc == 0 || n_qt == 0) return cudaSuccess;
-  return launch_tc(lib, b, lib_op, q_op, n_tc, n_qt, num_sms, timeout_s, s);
+  if (chunk <= 0) chunk = tc_default_chunk(fmt);
+  return fmt == kTcFp4 ? launch_tc<Fp4>(lib, b, lib_op, q_op, n_qt, num_sms, chunk, timeout_s, s)
+                       : launch_tc<Fp8>(lib, b, lib_op, q_op, n_qt, num_sms, chunk, timeout_s, s);
 }
+
+// Library tiles per work item: 64 x 256 records (FP8), 96 x 192 records (FP4) -- about
+// 16 K records, so that the query tiles of a chunk reuse it from L2.
+int tc_default_chunk(int fmt) { return fmt == kTcFp4 ? 96 : 64; }
 
 }  // namespace fps

@@ -31,7 +31,7 @@ K_SINGLE, Q_SINGLE = 30, 16
 def full(gpu_lib):
     fps = gpu_lib
     packed = synth.packed(N, 0)
-    lib = fps.fps_library_load(packed=packed, flags=fps.FPS_LOAD_TC_OPERAND)
+    lib = fps.fps_library_load(packed=packed, flags=fps.FPS_LOAD_TC_OPERAND | fps.FPS_LOAD_TC_FP4)
     raw = torch.from_numpy(packed.view(np.uint8).reshape(N, 24)).cuda()
     try:
         yield fps, lib, packed, raw
@@ -101,7 +101,8 @@ def test_single_query_step_full_size(full):
 
 def test_batched_paths_full_size(full):
     """The batched benchmark: 4096 generated queries (seed 1002), k drawn from {1, 10, 30, 100, 1000},
-    on the tensor cores and on the popcount path; a sample of 256 queries against the brute force."""
+    on the tensor cores (FP8 and FP4 operands) and on the popcount path; a sample of 256 queries
+    against the brute force."""
     fps, lib, packed, raw = full
     Q = 4096
     qs = synth.packed(Q, synth.query_seed(2))
@@ -110,6 +111,7 @@ def test_batched_paths_full_size(full):
     well_formed(tc, ks)
     pb = run_batch(fps, lib, qs, ks, fps.FPS_PATH_POPC_BATCH)
     equal(tc, pb)
+    equal(run_batch(fps, lib, qs, ks, fps.FPS_PATH_TC_FP4), pb)
     for q in range(0, Q, 8):
         oracle_distances_agree(packed, qs[q], *tc[q])
     sample = np.arange(7, Q, 16)
@@ -150,7 +152,7 @@ def test_largest_k_full_size(full):
     qs = np.concatenate([synth.packed(2, 1005), synth.packed_at([12345], 0)])
     ks = np.full(len(qs), k, np.int32)
     want = brute_topk(raw, qs, k)
-    for path in (fps.FPS_PATH_POPC, fps.FPS_PATH_POPC_BATCH, fps.FPS_PATH_TC_FP8):
+    for path in (fps.FPS_PATH_POPC, fps.FPS_PATH_POPC_BATCH, fps.FPS_PATH_TC_FP8, fps.FPS_PATH_TC_FP4):
         res = run_batch(fps, lib, qs, ks, path)
         well_formed(res, ks)
         for q, (gi, gd) in enumerate(res):

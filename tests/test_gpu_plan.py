@@ -113,6 +113,6 @@ def test_autotuner_caches_a_choice_per_size_class(gpu_lib):
                 for (gi, gd), (wi, wd) in zip(got, want):
                     assert np.array_equal(gi, wi) and np.array_equal(gd, wd)
                 seen.add(st.path_used)
-            assert seen <= {fps.FPS_PATH_POPC_BATCH, fps.FPS_PATH_TC_FP8}
+            assert seen <= {fps.FPS_PATH_POPC, fps.FPS_PATH_POPC_BATCH, fps.FPS_PATH_TC_FP8}
     finally:
         fps.fps_release(lib)

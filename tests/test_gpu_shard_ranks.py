@@ -53,12 +53,12 @@ def _rank(rank, world, port, path_code, out_path):
     bufs = [torch.zeros((3, int(s.item())), dtype=torch.int64) for s in sizes]
     dist.all_gather(bufs, mine)
     if rank == 0:
-        merged = []
+        merged = {}
         for q in range(Q):
             parts = [(b[1][b[0] == q].numpy().astype(np.int32), b[2][b[0] == q].numpy().astype(np.int32))
                      for b in bufs]
-            merged.append(np.stack(fps.fps_merge_topk(parts, int(KS[q]))))
-        np.save(out_path, np.array(merged, dtype=object), allow_pickle=True)
+            merged[f"i{q}"], merged[f"d{q}"] = fps.fps_merge_topk(parts, int(KS[q]))
+        np.savez(out_path, **merged)
     dist.destroy_process_group()
 
 
@@ -67,12 +67,12 @@ def test_two_ranks_search_their_halves_and_merge(gpu_lib, tmp_path, path_name):
     import torch.multiprocessing as mp
 
     fps = gpu_lib
-    out = str(tmp_path / "merged.npy")
+    out = str(tmp_path / "merged.npz")
     mp.start_processes(_rank, args=(2, _free_port(), getattr(fps, "FPS_PATH_" + path_name), out), nprocs=2,
                        join=True, start_method="spawn")
-    got = np.load(out, allow_pickle=True)
+    got = np.load(out)
     text = synth.text(N, 64)
     want = oracle.topk_many(text, synth.packed_to_strings(synth.packed(Q, 1064)), KS)
     for q in range(Q):
-        assert got[q][0].tolist() == want[q][0].tolist(), q
-        assert got[q][1].tolist() == want[q][1].tolist(), q
+        assert got[f"i{q}"].tolist() == want[q][0].tolist(), q
+        assert got[f"d{q}"].tolist() == want[q][1].tolist(), q

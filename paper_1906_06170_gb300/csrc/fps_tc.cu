@@ -70,7 +70,8 @@ constexpr int kEpiWarps = 8;                 // two per TMEM lane quarter
 constexpr int kFlushWarps = 2;               // drain the hand-off ring, alternate 32-slot blocks
 constexpr int kFlushWarp0 = 2 + kEpiWarps;   // first flusher
 constexpr int kRefWarp = kFlushWarp0 + kFlushWarps;   // re-derives query bounds from the histograms
-constexpr int kThreads = 32 * (kRefWarp + 1);
+constexpr int kMma2Warp = kRefWarp + 1;      // second MMA issuer (odd tiles; warp 1 takes the even ones)
+constexpr int kThreads = 32 * (kMma2Warp + 1);
 constexpr uint32_t kRefCap = 32;             // pending bound refreshes per flusher
 constexpr uint32_t kRingCap = 192;           // epilogue hand-offs in flight per CTA
 static_assert(kRingCap % (32 * kFlushWarps) == 0, "ring blocks alternate between the flushers");
@@ -84,7 +85,7 @@ struct Fp8 {
   static constexpr int kKBytes = 192;
   static constexpr int kMmaK = 32;
   static constexpr int kBStages = 3;
-  static constexpr int kBParts = 3;
+  static constexpr int kBParts = 1;
   static constexpr bool kFp4 = false;
   static constexpr uint32_t kAccStride = 256;   // TMEM columns between the two accumulators
 };
@@ -93,7 +94,7 @@ struct Fp4 {
   static constexpr int kKBytes = 96;
   static constexpr int kMmaK = 64;
   static constexpr int kBStages = 6;
-  static constexpr int kBParts = 2;
+  static constexpr int kBParts = 1;
   static constexpr bool kFp4 = true;
   static constexpr uint32_t kAccStride = 256;   // accumulators at columns 0 and 256, 192 wide
   static constexpr uint32_t kSfaCol = 192;      // scale factors beside them (every byte 127: scale 1)
@@ -385,7 +386,7 @@ struct TcSmem {
   uint64_t b_full[F::kBStages], b_empty[F::kBStages];
   uint64_t a_full[2], a_empty[2];
   uint64_t acc_full[2], acc_empty[2];
-  uint64_t fin;
+  uint64_t fin[2];                 // per MMA issuer: all of its MMAs complete
   uint32_t tmem_base;
   int bpos[kNumBuckets + 1];       // first layout position of each bucket
   int bend[kNumBuckets + 1];       // one past its last record
@@ -495,7 +496,7 @@ __device__ __forceinline__ uint32_t max32_u32(const uint32_t (&v)[32]) {
 template <class F>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_scan_kernel(DevLib lib, BatchDev b, const uint8_t* __restrict__ lib_op, const uint8_t* __restrict__ q_op,
-                   int64_t n_tc, int n_qt, int chunk, uint64_t timeout_ns) {
+                   int64_t n_tc, int stride, int n_qt, int chunk, uint64_t timeout_ns) {
   using G = Geom<F>;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   TcSmem<F>& S = *reinterpret_cast<TcSmem<F>*>(smem_raw);
@@ -514,11 +515,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&S.a_full[i], 1);
-      mbar_init(&S.a_empty[i], 1);
+      mbar_init(&S.a_empty[i], 2);   // both MMA issuers are done with the query tile
       mbar_init(&S.acc_full[i], 1);
       mbar_init(&S.acc_empty[i], kEpiWarps);
     }
-    mbar_init(&S.fin, 1);
+    mbar_init(&S.fin[0], 1);
+    mbar_init(&S.fin[1], 1);
     S.r_tail = 0;
     for (int f = 0; f < kFlushWarps; ++f) {
       S.f_head[f] = 32u * f;
@@ -582,7 +584,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         bulk_g2s(S.a[ab], q_op + static_cast<size_t>(qt) * G::kATileBytes, G::kATileBytes, &S.a_full[ab]);
         ++na;
         const int64_t t0 = c * chunk, t1 = min(t0 + chunk, n_tc);
-        for (int64_t T = t0; T < t1; ++T, ++bn) {
+        for (int64_t v = t0; v < t1; ++v, ++bn) {
+          const int64_t T = v * stride;
           const int s = static_cast<int>(bn % F::kBStages);
           const uint32_t use = bn / F::kBStages;
           if (!mbar_wait(&S.b_empty[s], (use & 1) ^ 1, deadline)) {
@@ -612,8 +615,14 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       if (!ok) atomicOr(b.err, DEVERR_TIMEOUT);
     }
-  } else if (warp == 1) {
+  } else if (warp == 1 || warp == kMma2Warp) {
     // ------------------------------------------------------------ MMA issue
+    // Two issuing threads, one per accumulator: warp 1 takes the even tiles of the
+    // CTA's sequence, warp kMma2Warp the odd ones.  Issuing a tcgen05.mma costs a
+    // single thread tens of cycles, as does each barrier wait, so one thread alone
+    // cannot keep the tensor pipe busy; with two, the MMAs of consecutive tiles are
+    // issued in parallel and run back to back.
+    const uint32_t mine = warp == 1 ? 0u : 1u;
     if (lane == 0) {
       const uint32_t idesc = instr_desc<F>();
       uint32_t sfa = 0, sfb = 0;
@@ -634,7 +643,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         tc_fence_after();
         const uint32_t a_base = smem_addr(S.a[ab]);
         const int64_t t0 = c * chunk, t1 = min(t0 + chunk, n_tc);
-        for (int64_t T = t0; T < t1; ++T, ++bn, ++tn) {
+        for (int64_t v = t0; v < t1; ++v, ++bn, ++tn) {
+          if ((tn & 1u) != mine) continue;
           const int s = static_cast<int>(bn % F::kBStages);
           const int acc = static_cast<int>(tn & 1);
           if (!mbar_wait(&S.acc_empty[acc], ((tn >> 1) & 1) ^ 1, deadline) ||
@@ -657,8 +667,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       if (!ok) atomicOr(b.err, DEVERR_TIMEOUT);
       // all MMAs issued by this thread complete before the final barrier
-      mma_commit(&S.fin);
-      mbar_wait(&S.fin, 0, drain);
+      mma_commit(&S.fin[mine]);
+      mbar_wait(&S.fin[mine], 0, drain);
     }
   } else if (warp < kFlushWarp0) {
     // -------------------------------------------------------------- epilogue
@@ -685,7 +695,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       // tile indices and layout positions fit 32 bits (positions index the int32 perm)
       const int t0 = static_cast<int>(c * chunk), t1 = static_cast<int>(min(c * chunk + chunk, n_tc));
-      bk = bucket_at(S.bpos, static_cast<int64_t>(t0) * F::kRows);
+      bk = bucket_at(S.bpos, static_cast<int64_t>(t0) * stride * F::kRows);
       // other CTAs' refreshes of this query reach the row through the global
       // bound, re-read every 8 tiles (loaded one tile before it is used)
       uint32_t gthr = thr;
@@ -700,7 +710,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (((T - t0) & 7) == 1) thr = gthr < thr ? gthr : thr;
           if (((T - t0) & 7) == 0) gthr = ld_relaxed_u32(b.thr + q);
         }
-        const int tpos = T * F::kRows;            // layout position of the tile's column 0
+        const int tpos = T * stride * F::kRows;   // layout position of the tile's column 0
         // a group of columns passes when acc >= ceil((pq + px - thr) / 2) for one of its
         // records: the largest accumulator against the bar of the group's bucket px
         auto bar_of = [&](int px, uint32_t& need16) {
@@ -1083,17 +1093,19 @@ int64_t tensor_tiles(int64_t n_tiles128) {
   return (n_tiles128 * kTile + F::kRows - 1) / F::kRows;
 }
 
+// stride > 1: only every stride-th library tile (a sample spread over all buckets).
 template <class F>
 cudaError_t launch_tc(const DevLib& lib, const BatchDev& b, const uint8_t* lib_op, const uint8_t* q_op, int n_qt,
-                      int num_sms, int chunk, double timeout_s, cudaStream_t s) {
-  const int64_t n_tc = tensor_tiles<F>(lib.n_tiles);
+                      int num_sms, int chunk, int stride, double timeout_s, cudaStream_t s) {
+  const int64_t n_all = tensor_tiles<F>(lib.n_tiles);
+  const int64_t n_tc = (n_all + stride - 1) / stride;
   if (n_tc == 0 || n_qt == 0) return cudaSuccess;
   const size_t smem = sizeof(TcSmem<F>) + 1024;
   static std::atomic<uint64_t> configured{0};
   cudaError_t e = smem_attr_once(tc_scan_kernel<F>, smem, &configured);
   if (e != cudaSuccess) return e;
   const uint64_t tns = static_cast<uint64_t>((timeout_s > 0 ? timeout_s : 2.0) * 1e9);
-  tc_scan_kernel<F><<<num_sms, kThreads, smem, s>>>(lib, b, lib_op, q_op, n_tc, n_qt, chunk, tns);
+  tc_scan_kernel<F><<<num_sms, kThreads, smem, s>>>(lib, b, lib_op, q_op, n_tc, stride, n_qt, chunk, tns);
   return cudaGetLastError();
 }
 
@@ -1141,11 +1153,12 @@ cudaError_t tc_pack_queries(int fmt, const uint64_t* q, int Q, uint8_t* op, cuda
 }
 
 cudaError_t tc_scan(int fmt, const DevLib& lib, const BatchDev& b, const uint8_t* lib_op, const uint8_t* q_op,
-                    int num_sms, int chunk, double timeout_s, cudaStream_t s) {
+                    int num_sms, int chunk, int stride, double timeout_s, cudaStream_t s) {
   const int n_qt = (b.Q + kTcQ - 1) / kTcQ;
   if (chunk <= 0) chunk = tc_default_chunk(fmt);
-  return fmt == kTcFp4 ? launch_tc<Fp4>(lib, b, lib_op, q_op, n_qt, num_sms, chunk, timeout_s, s)
-                       : launch_tc<Fp8>(lib, b, lib_op, q_op, n_qt, num_sms, chunk, timeout_s, s);
+  if (stride < 1) stride = 1;
+  return fmt == kTcFp4 ? launch_tc<Fp4>(lib, b, lib_op, q_op, n_qt, num_sms, chunk, stride, timeout_s, s)
+                       : launch_tc<Fp8>(lib, b, lib_op, q_op, n_qt, num_sms, chunk, stride, timeout_s, s);
 }
 
 // Library tiles per work item: 64 x 256 records (FP8), 96 x 192 records (FP4) -- about

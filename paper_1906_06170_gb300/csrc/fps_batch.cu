@@ -513,49 +513,3 @@ cudaError_t launch_progress(int64_t* slot_dev, int64_t value, cudaStream_t s) {
 
 }  // namespace fps
 
-namespace fps {
-namespace {
-
-// One warp per query: the smallest D <= thr with at least k accepted records at distance <= D
-// (a warp prefix sum over the histogram), then the query's histogram and count are cleared.
-__global__ void batch_rebound_kernel(BatchDev b) {
-  const int q = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (q >= b.Q) return;
-  const uint32_t k = b.k[q] > 0 ? static_cast<uint32_t>(b.k[q]) : 0u;
-  const uint32_t tcur = b.thr[q];
-  uint32_t* hist = b.hist + static_cast<size_t>(q) * 168;
-  uint32_t carry = 0, D = 0xFFFFFFFFu;
-  for (uint32_t base = 0; k > 0 && base <= tcur && base < 168u; base += 32) {
-    const uint32_t e = base + lane;
-    uint32_t x = (e <= tcur && e < 168u) ? hist[e] : 0u;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(kFull, x, o);
-      if (lane >= o) x += y;
-    }
-    const uint32_t hit = __ballot_sync(kFull, e <= tcur && e < 168u && carry + x >= k);
-    if (hit) {
-      D = base + static_cast<uint32_t>(__ffs(hit) - 1);
-      break;
-    }
-    carry += __shfl_sync(kFull, x, 31);
-  }
-  __syncwarp();
-  if (lane == 0) {
-    if (D < tcur) b.thr[q] = D;
-    b.cnt[q] = 0u;
-  }
-  for (int i = lane; i < 168; i += 32) hist[i] = 0u;
-}
-
-}  // namespace
-
-cudaError_t batch_rebound(const BatchDev& b, cudaStream_t s) {
-  if (b.Q == 0) return cudaSuccess;
-  constexpr int kWarps = 8;
-  batch_rebound_kernel<<<(b.Q + kWarps - 1) / kWarps, 32 * kWarps, 0, s>>>(b);
-  return cudaGetLastError();
-}
-
-}  // namespace fps

@@ -673,18 +673,6 @@ int tile_param_of(int path, int param) {
   return path == FPS_PATH_POPC_BATCH ? kPopcBatchDefaultQB : 0;
 }
 
-// Tensor-core batches without predicted bounds first scan every kPrepassStride-th library
-// tile (a sample spread over all popcount buckets) and take each query's exact k-th distance
-// over that sample as its bound (batch_rebound), then scan the whole library from there.  The
-// sampled pilot alone leaves large-k queries with loose bounds for the first part of the full
-// scan, where many records pass and queue at the epilogue's hand-off; a 1/32 sample costs 1/32
-// of a scan.  Libraries of fewer than 64 sample tiles skip it.
-constexpr int kPrepassStride = 32;
-
-bool use_prepass(const Library* L, int path, bool learned) {
-  return is_tc_path(path) && !learned && tc_tiles(tc_fmt_of(path), L->n_tiles) >= 64 * kPrepassStride;
-}
-
 // The device work of one batch: bounds (sampled or predicted), scan, per-query select.
 // path: FPS_PATH_POPC_BATCH, FPS_PATH_TC_FP8 or FPS_PATH_TC_FP4; param: its tile parameter.
 cudaError_t enqueue_batch(Library* L, const BatchDev& b, char* db, const BatchLayout& l, int path, int param,
@@ -696,12 +684,7 @@ cudaError_t enqueue_batch(Library* L, const BatchDev& b, char* db, const BatchLa
       const int fmt = tc_fmt_of(path);
       uint8_t* qop = reinterpret_cast<uint8_t*>(db + l.d_qop);
       ce = tc_pack_queries(fmt, b.queries, b.Q, qop, s);
-      if (ce == cudaSuccess && use_prepass(L, path, tau_dev != nullptr)) {
-        ce = tc_scan(fmt, L->dev, b, tc_operand_of(L, path), qop, L->num_sms, param, kPrepassStride, tmo, s);
-        if (ce == cudaSuccess) ce = batch_rebound(b, s);
-      }
-      if (ce == cudaSuccess)
-        ce = tc_scan(fmt, L->dev, b, tc_operand_of(L, path), qop, L->num_sms, param, 1, tmo, s);
+      if (ce == cudaSuccess) ce = tc_scan(fmt, L->dev, b, tc_operand_of(L, path), qop, L->num_sms, param, tmo, s);
     } else {
       ce = batch_scan_popc(L->dev, b, L->num_sms, reinterpret_cast<uint32_t*>(db + l.d_work), param, s);
     }

@@ -168,10 +168,6 @@ cudaError_t batch_scan_popc(const DevLib& lib, const BatchDev& b, int num_sms, u
                             cudaStream_t s);
 constexpr int kPopcBatchDefaultQB = 64;
 cudaError_t batch_select(const DevLib& lib, const BatchDev& b, cudaStream_t s);
-// After a scan of a sample of the library: thr[q] = min(thr[q], smallest D with at least k[q]
-// accepted records at distance <= D) -- a bound on the whole library's k-th distance, since
-// those records belong to it -- then the histograms and candidate counts start again from zero.
-cudaError_t batch_rebound(const BatchDev& b, cudaStream_t s);
 
 // ---- shard merge (fps_batch.cu): per-shard result lists of one batch (device memory, laid out
 // by the batch's output offsets) and the global index of each shard's first record
@@ -242,10 +238,9 @@ size_t tc_operand_bytes(int fmt, int64_t n_tiles128);
 size_t tc_query_operand_bytes(int fmt, int Q);
 cudaError_t tc_pack_library(int fmt, const DevLib& lib, uint8_t* op, cudaStream_t s);
 cudaError_t tc_pack_queries(int fmt, const uint64_t* q, int Q, uint8_t* op, cudaStream_t s);
-// chunk: library tiles per work item (<= 0: the format's default); stride > 1: only every
-// stride-th library tile (a sample spread over all popcount buckets)
+// chunk: library tiles per work item (<= 0: the format's default)
 cudaError_t tc_scan(int fmt, const DevLib& lib, const BatchDev& b, const uint8_t* lib_op, const uint8_t* q_op,
-                    int num_sms, int chunk, int stride, double timeout_s, cudaStream_t s);
+                    int num_sms, int chunk, double timeout_s, cudaStream_t s);
 int tc_default_chunk(int fmt);
 
 // Description of one search for the indirect scan launch (device memory).  The device-side

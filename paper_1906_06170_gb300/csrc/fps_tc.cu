@@ -475,6 +475,35 @@ __device__ __forceinline__ uint32_t half2_bits(uint32_t lo, uint32_t hi) {
   return *reinterpret_cast<const uint32_t*>(&h);
 }
 
+// FP16 and FP32 bit patterns of an integer 1 <= n < 1024 (both exact), with integer
+// arithmetic only: the exponent is the position of the top bit.
+__device__ __forceinline__ uint32_t f16_bits_of(int n) {
+  const int e = 31 - __clz(n);
+  return (static_cast<uint32_t>(e + 15) << 10) | ((static_cast<uint32_t>(n) << (10 - e)) & 0x3FFu);
+}
+__device__ __forceinline__ uint32_t f32_bits_of(int n) {
+  const int e = 31 - __clz(n);
+  return (static_cast<uint32_t>(e + 127) << 23) | ((static_cast<uint32_t>(n) << (23 - e)) & 0x7FFFFFu);
+}
+
+// Largest of the 64 non-negative FP16 values held as 32 pairs: four independent
+// max chains, then one fold (bit patterns of non-negative FP16 order like integers).
+__device__ __forceinline__ uint32_t max64_half(const uint32_t (&w)[32]) {
+  uint32_t m0 = __vimax3_u16x2(w[0], w[1], w[2]), m1 = __vimax3_u16x2(w[3], w[4], w[5]);
+  uint32_t m2 = __vimax3_u16x2(w[6], w[7], w[8]), m3 = __vimax3_u16x2(w[9], w[10], w[11]);
+#pragma unroll
+  for (int e = 12; e < 28; e += 8) {
+    m0 = __vimax3_u16x2(m0, w[e], w[e + 1]);
+    m1 = __vimax3_u16x2(m1, w[e + 2], w[e + 3]);
+    m2 = __vimax3_u16x2(m2, w[e + 4], w[e + 5]);
+    m3 = __vimax3_u16x2(m3, w[e + 6], w[e + 7]);
+  }
+  m0 = __vimax3_u16x2(m0, w[28], w[29]);
+  m1 = __vimax3_u16x2(m1, w[30], w[31]);
+  const uint32_t m = __vimax3_u16x2(m0, m1, __vmaxu2(m2, m3));
+  return max(m & 0xFFFFu, m >> 16);
+}
+
 // Largest of 32 non-negative FP32 bit patterns (they order like unsigned integers):
 // four independent max chains, then one fold, so the result is ready a few
 // instructions after the loads.
@@ -496,7 +525,7 @@ __device__ __forceinline__ uint32_t max32_u32(const uint32_t (&v)[32]) {
 template <class F>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_scan_kernel(DevLib lib, BatchDev b, const uint8_t* __restrict__ lib_op, const uint8_t* __restrict__ q_op,
-                   int64_t n_tc, int stride, int n_qt, int chunk, uint64_t timeout_ns) {
+                   int64_t n_tc, int n_qt, int chunk, uint64_t timeout_ns) {
   using G = Geom<F>;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   TcSmem<F>& S = *reinterpret_cast<TcSmem<F>*>(smem_raw);
@@ -584,8 +613,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         bulk_g2s(S.a[ab], q_op + static_cast<size_t>(qt) * G::kATileBytes, G::kATileBytes, &S.a_full[ab]);
         ++na;
         const int64_t t0 = c * chunk, t1 = min(t0 + chunk, n_tc);
-        for (int64_t v = t0; v < t1; ++v, ++bn) {
-          const int64_t T = v * stride;
+        for (int64_t T = t0; T < t1; ++T, ++bn) {
           const int s = static_cast<int>(bn % F::kBStages);
           const uint32_t use = bn / F::kBStages;
           if (!mbar_wait(&S.b_empty[s], (use & 1) ^ 1, deadline)) {
@@ -643,7 +671,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         tc_fence_after();
         const uint32_t a_base = smem_addr(S.a[ab]);
         const int64_t t0 = c * chunk, t1 = min(t0 + chunk, n_tc);
-        for (int64_t v = t0; v < t1; ++v, ++bn, ++tn) {
+        for (int64_t T = t0; T < t1; ++T, ++bn, ++tn) {
           if ((tn & 1u) != mine) continue;
           const int s = static_cast<int>(bn % F::kBStages);
           const int acc = static_cast<int>(tn & 1);
@@ -695,28 +723,38 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       // tile indices and layout positions fit 32 bits (positions index the int32 perm)
       const int t0 = static_cast<int>(c * chunk), t1 = static_cast<int>(min(c * chunk + chunk, n_tc));
-      bk = bucket_at(S.bpos, static_cast<int64_t>(t0) * stride * F::kRows);
-      // other CTAs' refreshes of this query reach the row through the global
-      // bound, re-read every 8 tiles (loaded one tile before it is used)
+      bk = bucket_at(S.bpos, static_cast<int64_t>(t0) * F::kRows);
+      int nxt = bk + 1 < kNumBuckets ? S.bpos[bk + 1] : 0x7FFFFFFF;   // where the next bucket starts
+      // the cursor moves only when a position reaches the next bucket (rarely: a few
+      // hundred boundaries in the whole library)
+      auto advance = [&](int p) {
+        while (p >= nxt) {
+          ++bk;
+          nxt = bk + 1 < kNumBuckets ? S.bpos[bk + 1] : 0x7FFFFFFF;
+        }
+      };
+      // other CTAs' refreshes of this query reach the row through the global bound,
+      // re-read every 16 tiles (loaded 8 tiles before it is used); the refresher's
+      // per-row word is read every 4 tiles
       uint32_t gthr = thr;
       for (int T = t0; T < t1; ++T, ++tn) {
         const int acc = static_cast<int>(tn & 1);
-        if (live) {   // the refresher may have tightened this row's bound
+        if (live && ((T - t0) & 3) == 0) {   // the refresher may have tightened this row's bound
           const unsigned long long w = *reinterpret_cast<volatile unsigned long long*>(&S.thr_w[row]);
           if ((w >> 32) == static_cast<unsigned long long>(j)) {
             const uint32_t t = 0xFFFFFFFFu - static_cast<uint32_t>(w);
             thr = t < thr ? t : thr;
           }
-          if (((T - t0) & 7) == 1) thr = gthr < thr ? gthr : thr;
-          if (((T - t0) & 7) == 0) gthr = ld_relaxed_u32(b.thr + q);
+          if (((T - t0) & 15) == 8) thr = gthr < thr ? gthr : thr;
+          if (((T - t0) & 15) == 0) gthr = ld_relaxed_u32(b.thr + q);
         }
-        const int tpos = T * stride * F::kRows;   // layout position of the tile's column 0
+        const int tpos = T * F::kRows;            // layout position of the tile's column 0
         // a group of columns passes when acc >= ceil((pq + px - thr) / 2) for one of its
         // records: the largest accumulator against the bar of the group's bucket px
         auto bar_of = [&](int px, uint32_t& need16) {
-          const int need = (pq + px - static_cast<int>(thr) + 1) >> 1;
-          need16 = need <= 0 ? 0u : static_cast<uint32_t>(__half_as_ushort(__int2half_rn(need)));
-          return need <= 0 ? 0u : __float_as_uint(static_cast<float>(need));
+          const int need = (pq + px - static_cast<int>(thr) + 1) >> 1;   // <= 166
+          need16 = need <= 0 ? 0u : f16_bits_of(need);
+          return need <= 0 ? 0u : f32_bits_of(need);
         };
         auto push = [&](auto&& fill, uint32_t need16, int px, int p0, int ncols) {
           int lim = S.bend[px] - p0;
@@ -733,7 +771,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         if constexpr (!F::kFp4) {
           // FP8: a 256-record tile lies inside one bucket; this warp reads columns
           // 128 half .. +127 as two groups of 64 FP16 values (pack::16b)
-          while (bk + 1 < kNumBuckets && S.bpos[bk + 1] <= tpos) ++bk;
+          advance(tpos);
           const bool act = live && static_cast<uint32_t>(abs(bk - pq)) <= thr;
           const bool landed = mbar_wait(&S.acc_full[acc], (tn >> 1) & 1, deadline);
           if (!__all_sync(kFull, landed)) {   // one verdict for the whole warp
@@ -757,13 +795,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             bar_of(bk, need16);
 #pragma unroll
             for (int g = 0; g < 2; ++g) {
-              uint32_t m = __vimax3_u16x2(v[g][0], v[g][1], v[g][2]);
-#pragma unroll
-              for (int e = 3; e < 31; e += 2) m = __vimax3_u16x2(m, v[g][e], v[g][e + 1]);
-              m = __vmaxu2(m, v[g][31]);
               // rare: some of these 64 records may be within the bound; the flusher
               // finishes the compare column by column
-              if (max(m & 0xFFFFu, m >> 16) >= need16) {
+              if (max64_half(v[g]) >= need16) {
                 auto fill = [&](RingEntry& e) {
 #pragma unroll
                   for (int i = 0; i < 8; ++i)
@@ -778,9 +812,9 @@ __global__ void __launch_bounds__(kThreads, 1)
           // columns); this warp reads group A = columns 64 half .. +63 and group B =
           // columns 128 + 32 half .. +31, each inside one bucket, as FP32 values
           const int pA = tpos + 64 * half, pB = tpos + 128 + 32 * half;
-          while (bk + 1 < kNumBuckets && S.bpos[bk + 1] <= pA) ++bk;
+          advance(pA);
           const int bkA = bk;
-          while (bk + 1 < kNumBuckets && S.bpos[bk + 1] <= pB) ++bk;
+          advance(pB);
           const int bkB = bk;
           const bool actA = live && static_cast<uint32_t>(abs(bkA - pq)) <= thr;
           const bool actB = live && static_cast<uint32_t>(abs(bkB - pq)) <= thr;
@@ -1093,19 +1127,17 @@ int64_t tensor_tiles(int64_t n_tiles128) {
   return (n_tiles128 * kTile + F::kRows - 1) / F::kRows;
 }
 
-// stride > 1: only every stride-th library tile (a sample spread over all buckets).
 template <class F>
 cudaError_t launch_tc(const DevLib& lib, const BatchDev& b, const uint8_t* lib_op, const uint8_t* q_op, int n_qt,
-                      int num_sms, int chunk, int stride, double timeout_s, cudaStream_t s) {
-  const int64_t n_all = tensor_tiles<F>(lib.n_tiles);
-  const int64_t n_tc = (n_all + stride - 1) / stride;
+                      int num_sms, int chunk, double timeout_s, cudaStream_t s) {
+  const int64_t n_tc = tensor_tiles<F>(lib.n_tiles);
   if (n_tc == 0 || n_qt == 0) return cudaSuccess;
   const size_t smem = sizeof(TcSmem<F>) + 1024;
   static std::atomic<uint64_t> configured{0};
   cudaError_t e = smem_attr_once(tc_scan_kernel<F>, smem, &configured);
   if (e != cudaSuccess) return e;
   const uint64_t tns = static_cast<uint64_t>((timeout_s > 0 ? timeout_s : 2.0) * 1e9);
-  tc_scan_kernel<F><<<num_sms, kThreads, smem, s>>>(lib, b, lib_op, q_op, n_tc, stride, n_qt, chunk, tns);
+  tc_scan_kernel<F><<<num_sms, kThreads, smem, s>>>(lib, b, lib_op, q_op, n_tc, n_qt, chunk, tns);
   return cudaGetLastError();
 }
 
@@ -1153,12 +1185,11 @@ cudaError_t tc_pack_queries(int fmt, const uint64_t* q, int Q, uint8_t* op, cuda
 }
 
 cudaError_t tc_scan(int fmt, const DevLib& lib, const BatchDev& b, const uint8_t* lib_op, const uint8_t* q_op,
-                    int num_sms, int chunk, int stride, double timeout_s, cudaStream_t s) {
+                    int num_sms, int chunk, double timeout_s, cudaStream_t s) {
   const int n_qt = (b.Q + kTcQ - 1) / kTcQ;
   if (chunk <= 0) chunk = tc_default_chunk(fmt);
-  if (stride < 1) stride = 1;
-  return fmt == kTcFp4 ? launch_tc<Fp4>(lib, b, lib_op, q_op, n_qt, num_sms, chunk, stride, timeout_s, s)
-                       : launch_tc<Fp8>(lib, b, lib_op, q_op, n_qt, num_sms, chunk, stride, timeout_s, s);
+  return fmt == kTcFp4 ? launch_tc<Fp4>(lib, b, lib_op, q_op, n_qt, num_sms, chunk, timeout_s, s)
+                       : launch_tc<Fp8>(lib, b, lib_op, q_op, n_qt, num_sms, chunk, timeout_s, s);
 }
 
 // Library tiles per work item: 64 x 256 records (FP8), 96 x 192 records (FP4) -- about

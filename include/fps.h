@@ -221,7 +221,9 @@ fps_status fps_search_packed(fps_library lib, const uint64_t* query, int k, int3
  * launch plan is made on the host); queries, out_index, out_dist and
  * out_count are host or device memory per opts->flags, as in
  * fps_search_packed.  opts->path selects the kernel (FPS_PATH_AUTO lets the
- * library choose).
+ * library choose).  Slots min(k[q], N) .. k[q] of each query hold -1; slots
+ * past k[q] are not written.  With a library of no records every path gives
+ * count 0 without launching a scan (stats->path_used = FPS_PATH_POPC).
  */
 fps_status fps_search_batch(fps_library lib, const uint64_t* queries, int Q, const int32_t* k,
                             const int64_t* out_offsets, int32_t* out_index, int32_t* out_dist, int32_t* out_count,
@@ -269,7 +271,8 @@ fps_status fps_search_noalloc(fps_library lib, const uint64_t* query, int k, int
  * single-query scan once per such query, reading the query, k and output
  * places from a device-side descriptor, so no host round trip is needed.  A
  * plan must not be run concurrently with itself; it must be released before
- * its library.
+ * its library.  A plan on a library of no records holds no device state; its
+ * runs write count 0 and -1 in each query's k slots on the host.
  */
 typedef struct fps_batch_plan_s* fps_batch_plan;
 fps_status fps_batch_plan_create(fps_library lib, int Q, const int32_t* k, int path, int learned, fps_batch_plan* out);

@@ -929,6 +929,11 @@ fps_status search_batch_impl(Library* L, const uint64_t* queries, int Q, const i
   if (!dev_io)
     for (int q = 0; q < Q; ++q)
       if (queries[3 * q + 2] >> (kBits - 128)) return FPS_ERR_INVALID_ARG;
+  if (path != FPS_PATH_AUTO && path != FPS_PATH_POPC && path != FPS_PATH_POPC_BATCH && !is_tc_path(path))
+    return FPS_ERR_UNSUPPORTED;   // FPS_PATH_TC_I8: sm_103a has no kind::i8
+  // no records: every path answers count 0 and -1 in each query's k slots, which the
+  // sequential path writes without launching a scan
+  if (L->n == 0) path = FPS_PATH_POPC;
   int param = 0;
   int64_t nf = 0;
   if (path == FPS_PATH_AUTO) {
@@ -973,8 +978,6 @@ fps_status search_batch_impl(Library* L, const uint64_t* queries, int Q, const i
     path = c.path;
     param = c.param;
   }
-  if (path != FPS_PATH_POPC && path != FPS_PATH_POPC_BATCH && !is_tc_path(path))
-    return FPS_ERR_UNSUPPORTED;   // FPS_PATH_TC_I8: sm_103a has no kind::i8
   if (!path_available(L, path)) return FPS_ERR_UNSUPPORTED;
   param = path == FPS_PATH_POPC ? 0 : tile_param_of(path, param);
   st = run_path(L, w, path, param, queries, Q, k, off, total, out_index, out_dist, out_count, opts, dev_io, s, tau,
@@ -997,6 +1000,7 @@ struct BatchPlan {
   int Q = 0;
   int path = FPS_PATH_POPC_BATCH, param = 0;   // batched kernel and its tile parameter
   bool learned = false;
+  bool empty = false;        // library without records: no device state, results written on the host
   std::vector<int32_t> k;
   std::vector<int64_t> off, coff;
   int64_t total = 0;
@@ -1665,6 +1669,11 @@ fps_status fps_batch_plan_create(fps_library lib, int Q, const int32_t* k, int p
     P->off[q + 1] = P->off[q] + k[q];
   }
   P->total = P->off[Q];
+  if (L->n == 0) {
+    P->empty = true;
+    *out = reinterpret_cast<fps_batch_plan>(P);
+    return FPS_OK;
+  }
   P->coff = batch_cand_offsets(k, Q, L->n);
   P->lay = batch_layout(Q, P->total, P->coff[Q], false, P->learned, qop_bytes_of(P->path, Q));
   DeviceGuard g(L->device);
@@ -1731,6 +1740,19 @@ fps_status fps_batch_plan_run(fps_batch_plan plan, const uint64_t* queries, cons
   for (int q = 0; q < P->Q; ++q)
     if (queries[3 * q + 2] >> (kBits - 128)) return FPS_ERR_INVALID_ARG;
   Library* L = P->L;
+  if (P->empty) {
+    for (int q = 0; q < P->Q; ++q) {
+      out_count[q] = 0;
+      fill_unused(out_index + P->off[q], out_dist + P->off[q], 0, P->k[q]);
+    }
+    if (stats) {
+      *stats = fps_search_stats{};
+      stats->queries = P->Q;
+      stats->path_used = P->path;
+      stats->tile_param = P->param;
+    }
+    return FPS_OK;
+  }
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   DeviceGuard g(L->device);
   if (!g.ok) return FPS_ERR_CUDA;

@@ -179,3 +179,59 @@ def test_wide_and_merge_slots(gpu_lib):
                                    od.ctypes.data, ctypes.byref(m)) == 0
     assert m.value == 3 and list(oi[:3]) == [0, 2, 5] and list(od[:3]) == [1, 2, 3]
     assert np.all(oi[3:] == -1) and np.all(od[3:] == -1)
+
+
+@pytest.mark.parametrize("path_name", ["POPC", "POPC_BATCH", "TC_FP8", "TC_FP4", "AUTO"])
+def test_empty_library_batch_slots(gpu_lib, path_name):
+    """A library of no records: every batched path returns count 0 and -1 in each query's k slots,
+    in the device form and the host form, without launching a scan; slots past k stay untouched."""
+    fps = gpu_lib
+    path = getattr(fps, "FPS_PATH_" + path_name)
+    lib = fps.fps_library_load(text=b"", flags=fps.FPS_LOAD_TC_OPERAND | fps.FPS_LOAD_TC_FP4)
+    try:
+        qs = synth.packed(4, 1023)
+        ks = np.array([3, 0, 30, 7], np.int32)
+        slack = 4
+        off = np.zeros(len(ks) + 1, np.int64)
+        off[1:] = np.cumsum(ks + slack)
+        qd = torch.from_numpy(qs.view(np.int64).copy()).cuda()
+        oi = torch.full((int(off[-1]),), SENT, dtype=torch.int32, device="cuda")
+        od = torch.full_like(oi, SENT)
+        oc = torch.full((len(ks),), SENT, dtype=torch.int32, device="cuda")
+        fps.fps_search_batch(lib, qd, ks, path=path, out_index=oi, out_dist=od, out_count=oc, offsets=off)
+        fps.fps_sync(lib)
+        dev = (oi.cpu().numpy(), od.cpu().numpy(), oc.cpu().numpy())
+        hi, hd = np.full(int(off[-1]), SENT, np.int32), np.full(int(off[-1]), SENT, np.int32)
+        hc = np.full(len(ks), SENT, np.int32)
+        o = fps.fps_search_opts()
+        o.path = path
+        assert fps._lib.fps_search_batch(lib._h, qs.ctypes.data, len(ks), ks.ctypes.data, off.ctypes.data,
+                                         hi.ctypes.data, hd.ctypes.data, hc.ctypes.data, ctypes.byref(o), None) == 0
+        for fi, fd, fc in (dev, (hi, hd, hc)):
+            assert np.all(fc == 0)
+            for q in range(len(ks)):
+                a = int(off[q])
+                assert np.all(fi[a: a + ks[q]] == -1) and np.all(fd[a: a + ks[q]] == -1), (path_name, q)
+                assert np.all(fi[a + ks[q]: off[q + 1]] == SENT) and np.all(fd[a + ks[q]: off[q + 1]] == SENT)
+    finally:
+        fps.fps_release(lib)
+
+
+def test_empty_library_plan(gpu_lib):
+    """A batch plan on a library of no records: each run writes count 0 and -1 in the k slots."""
+    fps = gpu_lib
+    lib = fps.fps_library_load(text=b"")
+    try:
+        ks = np.array([5, 0, 17], np.int32)
+        plan = fps.fps_batch_plan_create(lib, ks)
+        try:
+            qs = synth.packed(len(ks), 1024)
+            for _ in range(2):
+                st = fps.fps_search_stats()
+                oi, od, oc, off = fps.fps_batch_plan_run(plan, qs, stats=st, flat=True)
+                assert np.all(oc == 0) and st.queries == len(ks)
+                assert np.all(oi[: off[-1]] == -1) and np.all(od[: off[-1]] == -1)
+        finally:
+            fps.fps_batch_plan_release(plan)
+    finally:
+        fps.fps_release(lib)

@@ -25,14 +25,17 @@
 //           one of two accumulators and commits to the stage-free and
 //           accumulator-full barriers;
 //   warps 2..9 epilogue: thread = query (TMEM lane), two warps per lane
-//           quarter, each reading half of the tile's columns (tcgen05.ld) with
-//           one wait.  The accumulator goes back to the MMA as soon as the
-//           values are in registers.  The test needs one number per (query,
-//           group of columns), because a group lies inside one popcount bucket:
+//           quarter, each taking half of the tile's columns.  The test needs
+//           one number per (query, group of columns), because a group lies
+//           inside one popcount bucket:
 //             d <= thr  <=>  acc >= ceil((popc q + popc x - thr) / 2),
 //           taken as a max over the groups' bit patterns (non-negative FP16
-//           and FP32 values order like unsigned integers).  A lane whose group
-//           passes hands it (as FP16), with the bar, to a shared ring;
+//           and FP32 values order like unsigned integers).  FP8: the FP16
+//           values are read (tcgen05.ld, pack::16b) with one wait and the
+//           accumulator goes back to the MMA before the compare.  FP4: the
+//           TMEM loads return the group maxima themselves (tcgen05.ld.red), and
+//           only a passing group is read as values, before the release.  A lane
+//           whose group passes hands it (as FP16), with the bar, to a shared ring;
 //   warps 10, 11 flushers, taking alternate 32-slot blocks of the ring: each
 //           finishes the compare of up to 32 ring entries per round (one lane
 //           per entry, 64 columns), takes each entry's candidate slots with one
@@ -251,6 +254,32 @@ __device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t (&v)[3
         "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
       : "r"(taddr)
       : "memory");
+}
+
+// Maxima of three runs of 32 consecutive 32-bit TMEM columns of this thread's lane
+// (starting at columns a, b and c), taken by the TMEM loads themselves (tcgen05.ld.red:
+// max over the loaded columns as unsigned integers; non-negative FP32 values order like
+// their bit patterns).  Six loads of 16 columns; the loaded values themselves are not
+// needed, so all six write the same 16 scratch registers.  Valid only after tmem_wait_ld().
+__device__ __forceinline__ void tmem_max3x32_nowait(uint32_t a, uint32_t b, uint32_t c, uint32_t& ma, uint32_t& mb,
+                                                    uint32_t& mc) {
+#define FPS_T16 "{t0, t1, t2, t3, t4, t5, t6, t7, t8, t9, t10, t11, t12, t13, t14, t15}"
+  uint32_t a1, b1, c1;
+  asm volatile(
+      "{\n .reg .b32 t<16>;\n"
+      " tcgen05.ld.red.sync.aligned.32x32b.x16.max.u32 " FPS_T16 ", %0, [%6];\n"
+      " tcgen05.ld.red.sync.aligned.32x32b.x16.max.u32 " FPS_T16 ", %1, [%7];\n"
+      " tcgen05.ld.red.sync.aligned.32x32b.x16.max.u32 " FPS_T16 ", %2, [%8];\n"
+      " tcgen05.ld.red.sync.aligned.32x32b.x16.max.u32 " FPS_T16 ", %3, [%9];\n"
+      " tcgen05.ld.red.sync.aligned.32x32b.x16.max.u32 " FPS_T16 ", %4, [%10];\n"
+      " tcgen05.ld.red.sync.aligned.32x32b.x16.max.u32 " FPS_T16 ", %5, [%11];\n}\n"
+      : "=r"(ma), "=r"(a1), "=r"(mb), "=r"(b1), "=r"(mc), "=r"(c1)
+      : "r"(a), "r"(a + 16), "r"(b), "r"(b + 16), "r"(c), "r"(c + 16)
+      : "memory");
+  ma = max(ma, a1);
+  mb = max(mb, b1);
+  mc = max(mc, c1);
+#undef FPS_T16
 }
 
 // 32 consecutive TMEM columns of this thread's lane := w.
@@ -504,24 +533,6 @@ __device__ __forceinline__ uint32_t max64_half(const uint32_t (&w)[32]) {
   return max(m & 0xFFFFu, m >> 16);
 }
 
-// Largest of 32 non-negative FP32 bit patterns (they order like unsigned integers):
-// four independent max chains, then one fold, so the result is ready a few
-// instructions after the loads.
-__device__ __forceinline__ uint32_t max32_u32(const uint32_t (&v)[32]) {
-  uint32_t m0 = __vimax3_u32(v[0], v[1], v[2]), m1 = __vimax3_u32(v[3], v[4], v[5]);
-  uint32_t m2 = __vimax3_u32(v[6], v[7], v[8]), m3 = __vimax3_u32(v[9], v[10], v[11]);
-#pragma unroll
-  for (int e = 12; e < 28; e += 8) {
-    m0 = __vimax3_u32(m0, v[e], v[e + 1]);
-    m1 = __vimax3_u32(m1, v[e + 2], v[e + 3]);
-    m2 = __vimax3_u32(m2, v[e + 4], v[e + 5]);
-    m3 = __vimax3_u32(m3, v[e + 6], v[e + 7]);
-  }
-  m0 = __vimax3_u32(m0, v[28], v[29]);
-  m1 = __vimax3_u32(m1, v[30], v[31]);
-  return __vimax3_u32(m0, m1, max(m2, m3));
-}
-
 template <class F>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_scan_kernel(DevLib lib, BatchDev b, const uint8_t* __restrict__ lib_op, const uint8_t* __restrict__ q_op,
@@ -716,9 +727,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       const bool live = q < b.Q && b.k[q] > 0;
       int pq = 0;
       uint32_t thr = 0;
+      int64_t co = 0;      // the query's candidate region: first key, keys
+      uint32_t ccap = 0;
       if (live) {
         pq = __popcll(b.queries[3 * q]) + __popcll(b.queries[3 * q + 1]) + __popcll(b.queries[3 * q + 2]);
         thr = ld_relaxed_u32(b.thr + q);
+        co = b.cand_off[q];
+        ccap = static_cast<uint32_t>(b.cand_off[q + 1] - co);
         atomicMax(&S.thr_w[row], (static_cast<unsigned long long>(j) << 32) | (0xFFFFFFFFu - thr));
       }
       // tile indices and layout positions fit 32 bits (positions index the int32 perm)
@@ -760,9 +775,6 @@ __global__ void __launch_bounds__(kThreads, 1)
           int lim = S.bend[px] - p0;
           lim = lim < ncols ? lim : ncols;
           if (lim <= 0) return;
-          // the query's candidate region (read here: passing groups are rare)
-          const int64_t co = b.cand_off[q];
-          const uint32_t ccap = static_cast<uint32_t>(b.cand_off[q + 1] - co);
           if (!ring_push(S, fill, static_cast<uint32_t>(q), need16 | (static_cast<uint32_t>(lim) << 16),
                          static_cast<uint32_t>(pq + px) | (static_cast<uint32_t>(j) << 9), static_cast<uint32_t>(p0),
                          static_cast<unsigned long long>(co), ccap, deadline))
@@ -824,46 +836,58 @@ __global__ void __launch_bounds__(kThreads, 1)
             break;
           }
           tc_fence_after();
-          // group A (64 columns) is read and tested first, then group B (32 columns): two
-          // waits, so that at most 64 accumulators are in registers at a time.  A passing
-          // group (rare) goes to the ring before the accumulator is released: keeping its
-          // FP16 pairs across the release does not fit the register budget
+          // The maxima of group A (two 32-column halves) and group B come from the TMEM
+          // loads themselves (tcgen05.ld.red), one wait for all three.  A group that passes
+          // (rare) is read again as values and goes to the ring before the accumulator is
+          // released: keeping its values across the release costs more than the wait.
           uint32_t needA16 = 0, needB16 = 0;
           const uint32_t needA = bar_of(bkA, needA16), needB = bar_of(bkB, needB16);
           if (__any_sync(kFull, actA || actB)) {
             const uint32_t base = tmem + lane_addr + static_cast<uint32_t>(acc) * F::kAccStride;
-            {
-              uint32_t v0[32], v1[32];
-              tmem_ld32_nowait(base + 64 * half, v0);
-              tmem_ld32_nowait(base + 64 * half + 32, v1);
-              tmem_wait_ld();
-              if (actA && max(max32_u32(v0), max32_u32(v1)) >= needA) {
+            uint32_t mA0, mA1, mB;
+            tmem_max3x32_nowait(base + 64 * half, base + 64 * half + 32, base + 128 + 32 * half, mA0, mA1, mB);
+            tmem_wait_ld();
+            const bool passA = actA && max(mA0, mA1) >= needA;
+            const bool passB = actB && mB >= needB;
+            if (__any_sync(kFull, passA)) {
+              uint32_t hA[32];   // FP16 pairs (column 2i low, 2i + 1 high), read 32 columns at a time
+              {
+                uint32_t v[32];
+                tmem_ld32_nowait(base + 64 * half, v);
+                tmem_wait_ld();
+#pragma unroll
+                for (int i = 0; i < 16; ++i) hA[i] = half2_bits(v[2 * i], v[2 * i + 1]);
+              }
+              {
+                uint32_t v[32];
+                tmem_ld32_nowait(base + 64 * half + 32, v);
+                tmem_wait_ld();
+#pragma unroll
+                for (int i = 0; i < 16; ++i) hA[16 + i] = half2_bits(v[2 * i], v[2 * i + 1]);
+              }
+              if (passA) {
                 auto fill = [&](RingEntry& e) {
 #pragma unroll
-                  for (int i = 0; i < 4; ++i) {
-                    e.v[i] = make_uint4(half2_bits(v0[8 * i], v0[8 * i + 1]), half2_bits(v0[8 * i + 2], v0[8 * i + 3]),
-                                        half2_bits(v0[8 * i + 4], v0[8 * i + 5]),
-                                        half2_bits(v0[8 * i + 6], v0[8 * i + 7]));
-                    e.v[4 + i] = make_uint4(half2_bits(v1[8 * i], v1[8 * i + 1]),
-                                            half2_bits(v1[8 * i + 2], v1[8 * i + 3]),
-                                            half2_bits(v1[8 * i + 4], v1[8 * i + 5]),
-                                            half2_bits(v1[8 * i + 6], v1[8 * i + 7]));
-                  }
+                  for (int i = 0; i < 8; ++i)
+                    e.v[i] = make_uint4(hA[4 * i], hA[4 * i + 1], hA[4 * i + 2], hA[4 * i + 3]);
                 };
                 push(fill, needA16, bkA, pA, 64);
               }
             }
-            {
-              uint32_t v2[32];
-              tmem_ld32_nowait(base + 128 + 32 * half, v2);
-              tmem_wait_ld();
-              if (actB && max32_u32(v2) >= needB) {
+            if (__any_sync(kFull, passB)) {
+              uint32_t hB[16];
+              {
+                uint32_t v[32];
+                tmem_ld32_nowait(base + 128 + 32 * half, v);
+                tmem_wait_ld();
+#pragma unroll
+                for (int i = 0; i < 16; ++i) hB[i] = half2_bits(v[2 * i], v[2 * i + 1]);
+              }
+              if (passB) {
                 auto fill = [&](RingEntry& e) {
 #pragma unroll
                   for (int i = 0; i < 4; ++i) {
-                    e.v[i] = make_uint4(half2_bits(v2[8 * i], v2[8 * i + 1]), half2_bits(v2[8 * i + 2], v2[8 * i + 3]),
-                                        half2_bits(v2[8 * i + 4], v2[8 * i + 5]),
-                                        half2_bits(v2[8 * i + 6], v2[8 * i + 7]));
+                    e.v[i] = make_uint4(hB[4 * i], hB[4 * i + 1], hB[4 * i + 2], hB[4 * i + 3]);
                     e.v[4 + i] = make_uint4(0u, 0u, 0u, 0u);
                   }
                 };

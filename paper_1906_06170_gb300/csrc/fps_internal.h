@@ -62,6 +62,8 @@ struct DevLib {
 // the initial values, so consecutive scans on one stream need no memset.
 // The first 16 bytes (the two thresholds) are fetched by the bulk copy of every
 // scan tile, so warps see tightened thresholds without a dependent load.
+constexpr int kScanSmallMaxBlocks = 256;   // largest grid of the small-library scan
+
 struct ScanState {
   unsigned long long thr_key;    // upper bound on the k-th key (d << 32 | index)
   uint32_t thr_d;                // upper bound on the k-th distance
@@ -71,6 +73,7 @@ struct ScanState {
   uint32_t pad1[2];
   uint32_t hist[168];            // accepted records per distance (distinct records)
   uint32_t queue[16 * 32];       // tail work queues: counter c at queue[32 c] (one 128-byte line each)
+  uint32_t bcnt[kScanSmallMaxBlocks];   // small-library scan: each block's candidate counts and bound
 };
 static_assert(sizeof(ScanState) % 16 == 0, "ScanState keeps 16-byte alignment");
 

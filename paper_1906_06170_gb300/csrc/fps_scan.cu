@@ -788,8 +788,414 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
   for (int c = tid; c < kQueues; c += blockDim.x) st->queue[32 * c] = 0u;
 }
 
+constexpr int kSmallWarps = 16, kSmallCap = 256;   // k <= 128
+constexpr int kLargeWarps = 8, kLargeCap = 2048;   // k <= 1920
+
+// ------------------------------------------------------------ small libraries
+// A library whose layout has at most kSmPer positions per thread of a grid of
+// kSmThreads-thread blocks (about 1.2 M records on 152 SMs) is scanned in one
+// wave, without the bucket order: with a dozen records per thread, the fixed
+// costs of the streaming kernel (visit-order tables, copy rings, running
+// bounds, two global atomics per block) are most of a query's time.
+//   1. thread t computes the distances of layout positions t, t + T, t + 2T, ...
+//      (T threads in the grid; consecutive threads read consecutive records of
+//      the word-major tiles, so the loads coalesce);
+//   2. the block histograms its distances and takes T_b, the smallest D with at
+//      least k of its records at distance <= D (every record if it holds fewer).
+//      The k-th distance T of the whole library is <= T_b for every block;
+//   3. the block writes its records below T_b (fewer than k) and those at T_b
+//      (as many as its region has room for) as keys d << 32 | index to its own
+//      region of the candidate array, and its counts and T_b to the scan state;
+//   4. the last block to finish reads every region.  The keys hold every record
+//      below T, and every record at T unless some block with T_b == T ran out of
+//      room, in which case the records at T are read again from the library.
+//      The k-th smallest candidate distance is T; the keys below it plus the
+//      smallest indices at T, sorted, are the answer (Fig. 3's first k rows).
+constexpr int kSmThreads = 512;
+constexpr int kSmPer = 16;                  // layout positions per thread
+constexpr int kSmMaxK = 128;                // largest k served
+constexpr int kSmRegion = 2048;             // keys per block: [0, kSmMaxK) below T_b, then those at T_b
+constexpr int kSmTieRoom = kSmRegion - kSmMaxK;
+constexpr int kSmTieCap = 16384;            // keys at T sorted in shared memory by the merge
+constexpr size_t kSmSmem = static_cast<size_t>(kSmMaxK + kSmTieCap) * sizeof(unsigned long long);
+static_assert(kSmRegion <= kSmallWarps * (kSmallCap - kTile), "a block's region fits the candidate array");
+
+// bcnt word of a block: keys below T_b (bits 0-7), keys at T_b written (bits 8-19),
+// T_b (bits 20-27; 255 when the block holds fewer than k records), room ran out (bit 31)
+__device__ __forceinline__ uint32_t sm_pack(uint32_t lt, uint32_t eq, uint32_t tb, bool over) {
+  return lt | (eq << 8) | (tb << 20) | (over ? 0x80000000u : 0u);
+}
+
+// Warp-aggregated append: the lanes with take write key to dst[counter++] in lane order
+// (one shared atomic for the warp); slots at or past cap are counted, not written.
+// Called by all 32 lanes together.
+__device__ __forceinline__ void warp_append(bool take, unsigned long long key, uint32_t* counter,
+                                            unsigned long long* dst, uint32_t cap, int lane) {
+  const uint32_t m = __ballot_sync(kFull, take);
+  if (m == 0) return;
+  const int lead = __ffs(m) - 1;
+  uint32_t base = 0;
+  if (lane == lead) base = atomicAdd(counter, static_cast<uint32_t>(__popc(m)));
+  base = __shfl_sync(kFull, base, lead);
+  if (take) {
+    const uint32_t p = base + static_cast<uint32_t>(__popc(m & lanemask_lt()));
+    if (p < cap) dst[p] = key;
+  }
+}
+
+// Distance of layout position p to the query, or 0xFF for a padding position.  No
+// branch depends on a load, so the loads of consecutive calls are all in flight together.
+__device__ __forceinline__ uint32_t sm_dist(const DevLib& lib, int64_t p, uint64_t q0, uint64_t q1, uint64_t q2) {
+  const uint64_t* w = lib.words + (p >> 7) * (kWords * kTile) + (p & (kTile - 1));
+  const uint64_t x0 = __ldg(w), x1 = __ldg(w + kTile), x2 = __ldg(w + 2 * kTile);
+  const int32_t idx = __ldg(lib.perm + p);
+  const uint32_t d = static_cast<uint32_t>(__popcll(x0 ^ q0) + __popcll(x1 ^ q1) + __popcll(x2 ^ q2));
+  return idx < 0 ? 0xFFu : d;
+}
+
+// Ascending bitonic sort of 32 x E keys held by one warp, key i = lane + 32 e in x[e] of
+// lane `lane` (E a power of two): partners in other lanes are exchanged by shuffles,
+// partners in the same lane by register swaps.
+template <int E>
+__device__ __forceinline__ void warp_sort_regs(unsigned long long (&x)[E], int lane) {
+  constexpr int n = 32 * E;
+#pragma unroll
+  for (int kk = 2; kk <= n; kk <<= 1) {
+#pragma unroll
+    for (int j = kk >> 1; j > 0; j >>= 1) {
+      if (j >= 32) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int pe = e ^ (j >> 5);
+          if (pe > e) {
+            const bool asc = ((lane + 32 * e) & kk) == 0;
+            const unsigned long long a = x[e], b = x[pe];
+            if ((a > b) == asc) {
+              x[e] = b;
+              x[pe] = a;
+            }
+          }
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int i = lane + 32 * e;
+          const unsigned long long y = __shfl_xor_sync(kFull, x[e], j);
+          const bool asc = (i & kk) == 0, lower = (lane & j) == 0;
+          const bool take_min = lower == asc;
+          x[e] = take_min ? (y < x[e] ? y : x[e]) : (y > x[e] ? y : x[e]);
+        }
+      }
+    }
+  }
+}
+
+// The merge of the small-library scan, by its last block.  keys: kSmMaxK + kSmTieCap
+// shared keys.
+__device__ void sm_merge(const DevLib& lib, int k, ScanState* st, const unsigned long long* __restrict__ cand,
+                         int32_t* out_idx, int32_t* out_dist, int32_t* out_count, uint32_t* err, uint64_t q0,
+                         uint64_t q1, uint64_t q2, unsigned long long* keys) {
+  __shared__ uint32_t bc[kScanSmallMaxBlocks];
+  __shared__ uint32_t s_T, s_cless, s_nfin, s_ntie, s_tover, s_cnt;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nb = static_cast<int>(gridDim.x);
+  const int k_eff = static_cast<int>(k < lib.n ? k : lib.n);
+  unsigned long long* fin = keys;              // the answer: keys below T, then the chosen ones at T
+  unsigned long long* ties = keys + kSmMaxK;   // keys at T
+  if (tid == 0) {
+    s_nfin = 0u;
+    s_ntie = 0u;
+    s_tover = 0xFFFFFFFFu;
+  }
+  __syncthreads();
+  for (int b = tid; b < nb; b += kSmThreads) {
+    const uint32_t w = __ldcg(&st->bcnt[b]);
+    bc[b] = w;
+    if (w >> 31) atomicMin(&s_tover, (w >> 20) & 0xFFu);   // a block whose keys at its T_b ran out of room
+  }
+  if (warp == kSmThreads / 32 - 1) {
+    // T = first distance whose running count reaches k_eff.  The blocks added their counts
+    // at distances <= their own T_b, so the histogram is exact up to min T_b >= T.
+    uint32_t carry = 0;
+    int T = kNumBuckets, cl = 0;
+    for (int c0 = 0; c0 < kNumBuckets; c0 += 32) {
+      const int b = c0 + lane;
+      const uint32_t v = b < kNumBuckets ? __ldcg(&st->hist[b]) : 0u;
+      uint32_t incl = v;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const uint32_t hit = __ballot_sync(kFull, b < kNumBuckets && carry + incl >= static_cast<uint32_t>(k_eff));
+      if (hit) {
+        const int f = __ffs(hit) - 1;
+        T = c0 + f;
+        cl = static_cast<int>(carry + __shfl_sync(kFull, incl - v, f));
+        break;
+      }
+      carry += __shfl_sync(kFull, incl, 31);
+    }
+    if (lane == 0) {
+      s_T = static_cast<uint32_t>(T);
+      s_cless = static_cast<uint32_t>(cl);
+    }
+  }
+  __syncthreads();
+  // Every region's keys, fn(key) for each: warp w reads regions w, w + 16, ..., ten at a
+  // time, 32 consecutive keys per load, the first 64 keys of each of the ten regions in
+  // flight together; keys past 64 in a region (records at T_b) are read 32 at a time.
+  constexpr int kWarps = kSmThreads / 32, kBatch = 10;
+  auto key_index = [](uint32_t i, uint32_t lt) { return i < lt ? i : kSmMaxK + (i - lt); };
+  auto for_each_key = [&](auto&& fn) {
+    for (int b0 = warp; b0 < nb; b0 += kWarps * kBatch) {
+      unsigned long long v[kBatch][2];
+#pragma unroll
+      for (int j = 0; j < kBatch; ++j) {
+        const int b = b0 + kWarps * j;
+        const uint32_t w = b < nb ? bc[b] : 0u, lt = w & 0xFFu, n = lt + ((w >> 8) & 0xFFFu);
+        const unsigned long long* reg = cand + static_cast<size_t>(b < nb ? b : 0) * kSmRegion;
+        v[j][0] = static_cast<uint32_t>(lane) < n ? __ldcg(reg + key_index(lane, lt)) : ~0ull;
+        v[j][1] = static_cast<uint32_t>(lane + 32) < n ? __ldcg(reg + key_index(lane + 32, lt)) : ~0ull;
+      }
+#pragma unroll
+      for (int j = 0; j < kBatch; ++j) {
+        if (v[j][0] != ~0ull) fn(v[j][0]);
+        if (v[j][1] != ~0ull) fn(v[j][1]);
+      }
+      for (int j = 0; j < kBatch; ++j) {
+        const int b = b0 + kWarps * j;
+        if (b >= nb) break;
+        const uint32_t w = bc[b], lt = w & 0xFFu, n = lt + ((w >> 8) & 0xFFFu);
+        const unsigned long long* reg = cand + static_cast<size_t>(b) * kSmRegion;
+        for (uint32_t i = 64u + lane; i < n; i += 32u) fn(__ldcg(reg + key_index(i, lt)));
+      }
+    }
+  };
+  __syncthreads();
+  const uint32_t T = s_T;
+  const int cless = static_cast<int>(s_cless);
+  const int need = k_eff - cless;   // smallest indices still needed at distance T
+  if (T >= static_cast<uint32_t>(kNumBuckets)) {
+    if (tid == 0) atomicOr(err, DEVERR_INTERNAL);   // fewer candidates than k: cannot happen
+  } else {
+    // keys at T come from the regions unless a block with T_b == T ran out of room for
+    // them; then from the library itself
+    const bool from_lib = s_tover == T;
+    const int64_t n_pos = lib.n_tiles * kTile;
+    auto for_each_tie = [&](auto&& fn) {
+      if (from_lib) {
+        for (int64_t p = tid; p < n_pos; p += kSmThreads)
+          if (sm_dist(lib, p, q0, q1, q2) == T)
+            fn((static_cast<unsigned long long>(T) << 32) | static_cast<uint32_t>(__ldg(lib.perm + p)));
+      } else {
+        for_each_key([&](unsigned long long key) {
+          if (static_cast<uint32_t>(key >> 32) == T) fn(key);
+        });
+      }
+    };
+    auto add = [](uint32_t* counter, unsigned long long* dst, uint32_t cap, unsigned long long key) {
+      const uint32_t p = atomicAdd(counter, 1u);
+      if (p < cap) dst[p] = key;
+    };
+    for_each_key([&](unsigned long long key) {
+      const uint32_t d = static_cast<uint32_t>(key >> 32);
+      if (d < T)
+        add(&s_nfin, fin, kSmMaxK, key);
+      else if (d == T && !from_lib)
+        add(&s_ntie, ties, kSmTieCap, key);
+    });
+    if (from_lib) for_each_tie([&](unsigned long long key) { add(&s_ntie, ties, kSmTieCap, key); });
+    __syncthreads();
+    if (tid == 0 && (s_nfin != static_cast<uint32_t>(cless) || s_ntie < static_cast<uint32_t>(need)))
+      atomicOr(err, DEVERR_INTERNAL);
+    const int ntie = static_cast<int>(s_ntie);
+    // the keys below T and those at T sorted together in one warp's registers when they fit
+    // in kSmMaxK; otherwise the need smallest indices at T are chosen first
+    const int nt = need > 0 ? ntie : 0;
+    const bool together = cless + nt <= kSmMaxK;
+    if (need > 0 && !together) {
+      if (ntie <= kSmThreads) {
+        // one key per thread: the need-th smallest index by bisection, each step one
+        // block-wide count; the need keys at or below it are the ones (indices differ)
+        const bool has = tid < ntie;
+        const unsigned long long mine = has ? ties[tid] : ~0ull;
+        const uint32_t my = static_cast<uint32_t>(mine);
+        uint32_t lo = 0, hi = static_cast<uint32_t>(lib.n - 1);
+        while (lo < hi) {
+          const uint32_t mid = lo + (hi - lo) / 2;
+          if (__syncthreads_count(has && my <= mid) >= need)
+            hi = mid;
+          else
+            lo = mid + 1;
+        }
+        warp_append(has && my <= lo, mine, &s_nfin, fin, kSmMaxK, lane);
+      } else if (ntie <= kSmTieCap) {
+        const int p2 = next_pow2(ntie);
+        {
+          for (int i = ntie + tid; i < p2; i += kSmThreads) ties[i] = ~0ull;
+          __syncthreads();
+          block_bitonic_sort(ties, p2);
+          for (int i = tid; i < need; i += kSmThreads) fin[cless + i] = ties[i];
+        }
+      } else {
+        // very many records at T: the need-th smallest index among them, by bisection
+        uint32_t lo = 0, hi = 0x7FFFFFFFu;
+        while (lo < hi) {
+          const uint32_t mid = lo + (hi - lo) / 2;
+          if (tid == 0) s_cnt = 0u;
+          __syncthreads();
+          uint32_t local = 0;
+          for_each_tie([&](unsigned long long key) { local += static_cast<uint32_t>(key) <= mid; });
+          atomicAdd(&s_cnt, local);
+          __syncthreads();
+          if (s_cnt >= static_cast<uint32_t>(need))
+            hi = mid;
+          else
+            lo = mid + 1;
+          __syncthreads();
+        }
+        if (tid == 0) s_nfin = static_cast<uint32_t>(cless);
+        __syncthreads();
+        for_each_tie([&](unsigned long long key) {
+          if (static_cast<uint32_t>(key) <= lo) add(&s_nfin, fin, kSmMaxK, key);
+        });
+      }
+    }
+    __syncthreads();
+    if (warp == 0) {
+      // element i = lane + 32 e: fin[0 .. cless) then ties[0 .. nt) (together), or fin[0 .. k_eff)
+      unsigned long long x[kSmMaxK / 32];
+#pragma unroll
+      for (int e = 0; e < kSmMaxK / 32; ++e) {
+        const int i = lane + 32 * e;
+        if (together)
+          x[e] = i < cless ? fin[i] : (i - cless < nt ? ties[i - cless] : ~0ull);
+        else
+          x[e] = i < k_eff ? fin[i] : ~0ull;
+      }
+      warp_sort_regs(x, lane);
+      // the answer is the k_eff smallest keys (keys are unique: distance, then index)
+#pragma unroll
+      for (int e = 0; e < kSmMaxK / 32; ++e) {
+        const int i = lane + 32 * e;
+        if (i < k_eff) {
+          out_idx[i] = static_cast<int32_t>(x[e] & 0xFFFFFFFFull);
+          out_dist[i] = static_cast<int32_t>(x[e] >> 32);
+        }
+      }
+      if (lane == 0) *out_count = k_eff;
+    }
+  }
+  // slots past min(k, N), up to k, hold -1
+  for (int i = k_eff + tid; i < k; i += kSmThreads) {
+    out_idx[i] = -1;
+    out_dist[i] = -1;
+  }
+  // restore the scan state for the next search on this workspace
+  for (int b = tid; b < nb; b += kSmThreads) st->bcnt[b] = 0u;
+  for (int b = tid; b < 168; b += kSmThreads) st->hist[b] = 0u;
+  if (tid == 0) st->done = 0u;
+}
+
+__global__ void __launch_bounds__(kSmThreads, 1)
+    scan_small_kernel(DevLib lib, const uint64_t* __restrict__ query, int k, ScanState* st,
+                      unsigned long long* __restrict__ cand, int32_t* __restrict__ out_idx,
+                      int32_t* __restrict__ out_dist, int32_t* __restrict__ out_count, uint32_t* err) {
+  extern __shared__ __align__(16) unsigned long long sm_keys[];   // merge: [below T][at T]
+  __shared__ uint32_t hist[168];
+  __shared__ uint32_t s_lt, s_eq, s_tb, s_last;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t n_pos = lib.n_tiles * kTile;
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * kSmThreads;
+  const int64_t g = static_cast<int64_t>(blockIdx.x) * kSmThreads + tid;
+  const uint64_t q0 = __ldg(query), q1 = __ldg(query + 1), q2 = __ldg(query + 2);
+  for (int b = tid; b < 168; b += kSmThreads) hist[b] = 0u;
+  if (tid == 0) {
+    s_lt = 0u;
+    s_eq = 0u;
+  }
+  // 1. distances, 8 bits each (0xFF: no record)
+  uint32_t dpk[kSmPer / 4];
+#pragma unroll
+  for (int i = 0; i < kSmPer / 4; ++i) dpk[i] = 0u;
+#pragma unroll
+  for (int i = 0; i < kSmPer; ++i) {
+    // positions past the layout read its last position (a valid address) and are dropped
+    const int64_t p = g + i * stride;
+    const uint32_t d = sm_dist(lib, p < n_pos ? p : n_pos - 1, q0, q1, q2);
+    dpk[i >> 2] |= (p < n_pos ? d : 0xFFu) << (8 * (i & 3));
+  }
+  __syncthreads();
+  // 2. the block's histogram (one shared atomic per distinct distance of a warp step)
+#pragma unroll
+  for (int i = 0; i < kSmPer; ++i) {
+    const uint32_t d = (dpk[i >> 2] >> (8 * (i & 3))) & 0xFFu;
+    const uint32_t same = __match_any_sync(kFull, d);
+    if (d != 0xFFu && (same & lanemask_lt()) == 0) atomicAdd(&hist[d], static_cast<uint32_t>(__popc(same)));
+  }
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t carry = 0, tb = 0xFFu;
+    for (int c0 = 0; c0 < kNumBuckets && tb == 0xFFu; c0 += 32) {
+      const int b = c0 + lane;
+      const uint32_t v = b < kNumBuckets ? hist[b] : 0u;
+      uint32_t incl = v;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const uint32_t hit = __ballot_sync(kFull, b < kNumBuckets && carry + incl >= static_cast<uint32_t>(k));
+      if (hit) tb = static_cast<uint32_t>(c0 + __ffs(hit) - 1);
+      carry += __shfl_sync(kFull, incl, 31);
+    }
+    if (lane == 0) s_tb = tb;
+  }
+  __syncthreads();
+  // 3. the block's counts at distances <= T_b to the global histogram (exact there for
+  // D <= min T_b, where the k-th distance lies), and its keys below T_b, then at T_b,
+  // into its region
+  const uint32_t tb = s_tb;
+  for (int b = tid; b < kNumBuckets && static_cast<uint32_t>(b) <= tb; b += kSmThreads)
+    if (hist[b]) red_add_u32(&st->hist[b], hist[b]);
+  unsigned long long* region = cand + static_cast<size_t>(blockIdx.x) * kSmRegion;
+#pragma unroll
+  for (int i = 0; i < kSmPer; ++i) {
+    const uint32_t d = (dpk[i >> 2] >> (8 * (i & 3))) & 0xFFu;
+    if (d <= tb && d != 0xFFu) {
+      const unsigned long long key =
+          (static_cast<unsigned long long>(d) << 32) | static_cast<uint32_t>(__ldg(lib.perm + g + i * stride));
+      if (d < tb) {
+        region[atomicAdd(&s_lt, 1u)] = key;   // fewer than k <= kSmMaxK
+      } else {
+        const uint32_t slot = atomicAdd(&s_eq, 1u);
+        if (slot < static_cast<uint32_t>(kSmTieRoom)) region[kSmMaxK + slot] = key;
+      }
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    const uint32_t eq = s_eq;
+    st->bcnt[blockIdx.x] = sm_pack(s_lt, min(eq, static_cast<uint32_t>(kSmTieRoom)), tb, eq > kSmTieRoom);
+  }
+  // one fence for the keys and the counts, then the count of finished blocks
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) s_last = atomicAdd(&st->done, 1u) == gridDim.x - 1 ? 1u : 0u;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  // in a sequence of searches, wait for the previous one to finish before the merge and
+  // let the next one start (see the streaming kernel)
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  sm_merge(lib, k, st, cand, out_idx, out_dist, out_count, err, q0, q1, q2, sm_keys);
+}
+
 __global__ void scan_state_init_kernel(ScanState* st) {
   for (int b = threadIdx.x; b < 168; b += blockDim.x) st->hist[b] = 0u;
+  for (int b = threadIdx.x; b < kScanSmallMaxBlocks; b += blockDim.x) st->bcnt[b] = 0u;
   if (threadIdx.x == 0) {
     st->thr_key = ~0ull;
     st->thr_d = 166u;
@@ -861,8 +1267,6 @@ __global__ void fallback_pick_kernel(const uint64_t* queries, const int32_t* k, 
   }
 }
 
-constexpr int kSmallWarps = 16, kSmallCap = 256;   // k <= 128
-constexpr int kLargeWarps = 8, kLargeCap = 2048;   // k <= 1920
 
 }  // namespace
 
@@ -900,9 +1304,36 @@ cudaError_t launch_fallback_pick(const uint64_t* queries, const int32_t* k, cons
   return cudaGetLastError();
 }
 
+bool scan_small_fits(const DevLib& lib, int k, int num_sms) {
+  return lib.n > 0 && k >= 1 && k <= kSmMaxK && num_sms >= 1 && num_sms <= kScanSmallMaxBlocks &&
+         lib.n_tiles * kTile <= static_cast<int64_t>(kSmPer) * num_sms * kSmThreads;
+}
+
+// The small-library scan has no waits (every load is a plain load), so it takes no deadline.
+cudaError_t launch_scan_small(const DevLib& lib, const uint64_t* q, int k, ScanState* st, unsigned long long* cand,
+                              int32_t* oi, int32_t* od, int32_t* oc, uint32_t* err, int num_sms, bool programmatic,
+                              cudaStream_t s) {
+  static std::atomic<uint64_t> configured{0};
+  cudaError_t ce = smem_attr_once(scan_small_kernel, kSmSmem, &configured);
+  if (ce != cudaSuccess) return ce;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(static_cast<unsigned>(num_sms));
+  cfg.blockDim = dim3(kSmThreads);
+  cfg.dynamicSmemBytes = kSmSmem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = programmatic ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, scan_small_kernel, lib, q, k, st, cand, oi, od, oc, err);
+}
+
 cudaError_t launch_scan_single(const DevLib& lib, const uint64_t* d_query, int k, ScanState* st,
                                unsigned long long* cand, int32_t* out_idx, int32_t* out_dist, int32_t* out_count,
                                uint32_t* err, int num_sms, double timeout_s, cudaStream_t s, bool programmatic) {
+  if (scan_small_fits(lib, k, num_sms))
+    return launch_scan_small(lib, d_query, k, st, cand, out_idx, out_dist, out_count, err, num_sms, programmatic, s);
   uint64_t tns = static_cast<uint64_t>((timeout_s > 0 ? timeout_s : 2.0) * 1e9);
   if (k <= kSmallCap - kTile)
     return launch_cfg<kSmallWarps, kSmallCap>(lib, d_query, k, st, cand, out_idx, out_dist, out_count, err, num_sms,

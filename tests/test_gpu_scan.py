@@ -208,3 +208,41 @@ def test_workload_one_million_exact(gpu_lib):
             check(fps, lib, text, q, 30)
     finally:
         fps.fps_release(lib)
+
+
+def test_small_library_scan_many_equal_distances(gpu_lib):
+    """Libraries that take the one-wave small-library scan (up to about 1.2 M records, k <= 128)
+    with so many records at one distance that a block's region cannot hold all of its records at
+    its own bound: the merge then reads the records at the k-th distance again from the library
+    (and, with more of them than it can sort, finds the smallest indices by bisection)."""
+    fps = gpu_lib
+    x = synth.packed_to_strings(synth.packed(3, 16))
+    q = synth.packed(1, 1016)[0]
+    cases = {
+        "identical_400k": [x[0]] * 400_000,
+        "identical_with_nearer_rows": [x[0]] * 150_000 + [x[1]] + [x[0]] * 150_000 + [x[2]] * 3 + [x[0]] * 50_000,
+    }
+    for name, rows in cases.items():
+        text = synth.strings_to_text(rows)
+        lib = fps.fps_library_load(text=text)
+        try:
+            for k in (1, 30, 128, 129):
+                check(fps, lib, text, q, k)
+            check(fps, lib, text, fps.fps_pack_query(rows[0]), 30, device_io=True)
+        finally:
+            fps.fps_release(lib)
+
+
+@pytest.mark.parametrize("k", [1, 30, 128, 129])
+def test_small_library_scan_at_its_size_limit(gpu_lib, k):
+    """1.2 M records: the largest libraries the one-wave scan takes on 152 SMs (k <= 128), and the
+    streaming scan beside it (k = 129)."""
+    fps = gpu_lib
+    n = 1_200_000
+    text = synth.text(n, 19)
+    lib = fps.fps_library_load(text=text)
+    try:
+        for s in (1019, 2019):
+            check(fps, lib, text, synth.packed(1, s)[0], k, device_io=(s == 2019))
+    finally:
+        fps.fps_release(lib)

@@ -942,18 +942,24 @@ __device__ void sm_merge(const DevLib& lib, int k, ScanState* st, const unsigned
     }
   }
   __syncthreads();
-  // Every region's keys, fn(key) for each: warp w reads regions w, w + 16, ..., ten at a
-  // time, 32 consecutive keys per load, the first 64 keys of each of the ten regions in
-  // flight together; keys past 64 in a region (records at T_b) are read 32 at a time.
+  // The keys that can hold the answer, fn(key) for each: a region's keys below its T_b,
+  // and its keys at T_b only when T_b == T (T <= T_b, so otherwise they lie above T).
+  // Warp w reads regions w, w + 16, ..., ten at a time, 32 consecutive keys per load, the
+  // first 64 keys of each of the ten regions in flight together; keys past 64 in a region
+  // are read 32 at a time.  Called once T is known.
   constexpr int kWarps = kSmThreads / 32, kBatch = 10;
   auto key_index = [](uint32_t i, uint32_t lt) { return i < lt ? i : kSmMaxK + (i - lt); };
+  auto keys_of = [&](uint32_t w) {
+    const uint32_t lt = w & 0xFFu;
+    return ((w >> 20) & 0xFFu) == s_T ? lt + ((w >> 8) & 0xFFFu) : lt;
+  };
   auto for_each_key = [&](auto&& fn) {
     for (int b0 = warp; b0 < nb; b0 += kWarps * kBatch) {
       unsigned long long v[kBatch][2];
 #pragma unroll
       for (int j = 0; j < kBatch; ++j) {
         const int b = b0 + kWarps * j;
-        const uint32_t w = b < nb ? bc[b] : 0u, lt = w & 0xFFu, n = lt + ((w >> 8) & 0xFFFu);
+        const uint32_t w = b < nb ? bc[b] : 0u, lt = w & 0xFFu, n = b < nb ? keys_of(w) : 0u;
         const unsigned long long* reg = cand + static_cast<size_t>(b < nb ? b : 0) * kSmRegion;
         v[j][0] = static_cast<uint32_t>(lane) < n ? __ldcg(reg + key_index(lane, lt)) : ~0ull;
         v[j][1] = static_cast<uint32_t>(lane + 32) < n ? __ldcg(reg + key_index(lane + 32, lt)) : ~0ull;
@@ -966,7 +972,7 @@ __device__ void sm_merge(const DevLib& lib, int k, ScanState* st, const unsigned
       for (int j = 0; j < kBatch; ++j) {
         const int b = b0 + kWarps * j;
         if (b >= nb) break;
-        const uint32_t w = bc[b], lt = w & 0xFFu, n = lt + ((w >> 8) & 0xFFFu);
+        const uint32_t w = bc[b], lt = w & 0xFFu, n = keys_of(w);
         const unsigned long long* reg = cand + static_cast<size_t>(b) * kSmRegion;
         for (uint32_t i = 64u + lane; i < n; i += 32u) fn(__ldcg(reg + key_index(i, lt)));
       }
@@ -1127,12 +1133,11 @@ __global__ void __launch_bounds__(kSmThreads, 1)
     dpk[i >> 2] |= (p < n_pos ? d : 0xFFu) << (8 * (i & 3));
   }
   __syncthreads();
-  // 2. the block's histogram (one shared atomic per distinct distance of a warp step)
+  // 2. the block's histogram of its distances
 #pragma unroll
   for (int i = 0; i < kSmPer; ++i) {
     const uint32_t d = (dpk[i >> 2] >> (8 * (i & 3))) & 0xFFu;
-    const uint32_t same = __match_any_sync(kFull, d);
-    if (d != 0xFFu && (same & lanemask_lt()) == 0) atomicAdd(&hist[d], static_cast<uint32_t>(__popc(same)));
+    if (d != 0xFFu) atomicAdd(&hist[d], 1u);
   }
   __syncthreads();
   if (warp == 0) {

@@ -158,10 +158,11 @@ def measured_peak_gbs():
 
 
 def scan_kernel_source_hash() -> str:
-    """Hash of the single-query scan's device code: fps_scan.cu up to its host-side launch code
-    (host-only edits further down leave the profiled kernel unchanged)."""
+    """Hash of the streaming single-query scan's device code: fps_scan.cu up to the section of
+    the small-library scan that follows it (edits further down -- the small-library kernel, the
+    host-side launch code -- leave the profiled kernel unchanged)."""
     text = open(SCAN_SRC, "rb").read()
-    cut = text.find(b"cudaError_t configure_cfg()")
+    cut = text.find(b"// ------------------------------------------------------------ small libraries")
     return hashlib.sha256(text[:cut if cut > 0 else len(text)]).hexdigest()[:16]
 
 

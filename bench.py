@@ -613,7 +613,7 @@ def run_latency(args):
     print(json.dumps(latency_entry(n, args.steps, args.warmup)), flush=True)
 
 
-TC_TILE_ROWS = {"fp8": 256, "fp4": 192}
+TC_TILE_ROWS = {"fp8": 256, "fp4": 128}
 
 
 def tc_padded_records(n_tiles128: int, fmt: str) -> int:

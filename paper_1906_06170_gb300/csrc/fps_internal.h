@@ -232,7 +232,7 @@ bool tune_cache_put(const char* path, const char* device, int64_t n, const std::
 
 // ---- tensor-core batched scan (fps_tc.cu)
 // Operand formats: 0/1 FP8 E4M3 bytes (kind::f8f6f4, 256-record tiles) or packed
-// FP4 E2M1 nibbles with unit block scales (kind::mxf4, 192-record tiles).
+// FP4 E2M1 nibbles with unit block scales (kind::mxf4, 128-record tiles).
 constexpr int kTcFp8 = 0;
 constexpr int kTcFp4 = 1;
 int64_t tc_tiles(int fmt, int64_t n_tiles128);         // library tiles of the format

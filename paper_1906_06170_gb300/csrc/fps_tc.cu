@@ -11,19 +11,20 @@
 //        integer up to 2048 is exact in FP16); tiles of 256 records;
 //   FP4  kind::mxf4 (block-scaled), packed E2M1 nibbles (0x2 = 1.0, two keys
 //        per byte), FP32 accumulators; every UE8M0 scale factor is 127
-//        (2^0 = 1), so each product is still 0 or 1; tiles of 192 records,
-//        because the scale factors need TMEM columns next to the two
-//        accumulators.  Half the operand bytes of FP8 per key.
+//        (2^0 = 1), so each product is still 0 or 1; tiles of 128 records,
+//        so that three accumulators (TMEM columns 0, 128, 256) and the scale
+//        factors fit the 512 columns.  Half the operand bytes of FP8 per key.
 // (sm_103a has no tcgen05 kind::i8, so there is no INT8 variant.)
 //
-// CTA (one per SM, 13 warps):
+// CTA (one per SM, 14 warps):
 //   warp 0  producer: 1-D bulk copies (cp.async.bulk) of the query tile A
 //           (128 rows, double-buffered per work item) and of library tiles B
 //           into a ring of stages, completing on mbarriers;
-//   warp 1  allocates 512 TMEM columns; one thread issues the MMAs of a
-//           library tile (K = 192 in slices of 32 (FP8) or 64 (FP4) keys) into
-//           one of two accumulators and commits to the stage-free and
-//           accumulator-full barriers;
+//   warps 1, 13  MMA issuers (warp 1 also allocates 512 TMEM columns): one
+//           thread of each issues the MMAs of alternate library tiles (K = 192
+//           in slices of 32 (FP8) or 64 (FP4) keys) into the tile's accumulator
+//           (two for FP8, three for FP4, in turn) and commits to the stage-free
+//           and accumulator-full barriers;
 //   warps 2..9 epilogue: thread = query (TMEM lane), two warps per lane
 //           quarter, each taking half of the tile's columns.  The test needs
 //           one number per (query, group of columns), because a group lies
@@ -33,9 +34,10 @@
 //           and FP32 values order like unsigned integers).  FP8: the FP16
 //           values are read (tcgen05.ld, pack::16b) with one wait and the
 //           accumulator goes back to the MMA before the compare.  FP4: the
-//           TMEM loads return the group maxima themselves (tcgen05.ld.red), and
-//           only a passing group is read as values, before the release.  A lane
-//           whose group passes hands it (as FP16), with the bar, to a shared ring;
+//           TMEM loads return the group maximum itself (tcgen05.ld.red), and
+//           only a passing group is read as values, before the release (the
+//           MMA meanwhile fills the other two accumulators).  A lane whose
+//           group passes hands it (as FP16), with the bar, to a shared ring;
 //   warps 10, 11 flushers, taking alternate 32-slot blocks of the ring: each
 //           finishes the compare of up to 32 ring entries per round (one lane
 //           per entry, 64 columns), takes each entry's candidate slots with one
@@ -90,17 +92,19 @@ struct Fp8 {
   static constexpr int kBStages = 3;
   static constexpr int kBParts = 1;
   static constexpr bool kFp4 = false;
+  static constexpr int kAccs = 2;                // accumulators in TMEM
   static constexpr uint32_t kAccStride = 256;   // TMEM columns between the two accumulators
 };
 struct Fp4 {
-  static constexpr int kRows = 192;
+  static constexpr int kRows = 128;
   static constexpr int kKBytes = 96;
   static constexpr int kMmaK = 64;
-  static constexpr int kBStages = 6;
+  static constexpr int kBStages = 8;
   static constexpr int kBParts = 1;
   static constexpr bool kFp4 = true;
-  static constexpr uint32_t kAccStride = 256;   // accumulators at columns 0 and 256, 192 wide
-  static constexpr uint32_t kSfaCol = 192;      // scale factors beside them (every byte 127: scale 1)
+  static constexpr int kAccs = 3;               // three accumulators, at columns 0, 128 and 256
+  static constexpr uint32_t kAccStride = 128;
+  static constexpr uint32_t kSfaCol = 384;      // scale factors beside them (every byte 127: scale 1)
   static constexpr uint32_t kSfbCol = 448;
   static constexpr int kSfCols = 64;
 };
@@ -256,30 +260,25 @@ __device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t (&v)[3
       : "memory");
 }
 
-// Maxima of three runs of 32 consecutive 32-bit TMEM columns of this thread's lane
-// (starting at columns a, b and c), taken by the TMEM loads themselves (tcgen05.ld.red:
-// max over the loaded columns as unsigned integers; non-negative FP32 values order like
-// their bit patterns).  Six loads of 16 columns; the loaded values themselves are not
-// needed, so all six write the same 16 scratch registers.  Valid only after tmem_wait_ld().
-__device__ __forceinline__ void tmem_max3x32_nowait(uint32_t a, uint32_t b, uint32_t c, uint32_t& ma, uint32_t& mb,
-                                                    uint32_t& mc) {
+// Largest of 64 consecutive 32-bit TMEM columns of this thread's lane, taken by the TMEM
+// loads themselves (tcgen05.ld.red: max over the loaded columns as unsigned integers;
+// non-negative FP32 values order like their bit patterns).  Four loads of 16 columns; the
+// loaded values are not needed, so all four write the same 16 scratch registers.  Valid
+// only after tmem_wait_ld().
+__device__ __forceinline__ uint32_t tmem_max64_nowait(uint32_t a) {
 #define FPS_T16 "{t0, t1, t2, t3, t4, t5, t6, t7, t8, t9, t10, t11, t12, t13, t14, t15}"
-  uint32_t a1, b1, c1;
+  uint32_t m0, m1, m2, m3;
   asm volatile(
       "{\n .reg .b32 t<16>;\n"
-      " tcgen05.ld.red.sync.aligned.32x32b.x16.max.u32 " FPS_T16 ", %0, [%6];\n"
-      " tcgen05.ld.red.sync.aligned.32x32b.x16.max.u32 " FPS_T16 ", %1, [%7];\n"
-      " tcgen05.ld.red.sync.aligned.32x32b.x16.max.u32 " FPS_T16 ", %2, [%8];\n"
-      " tcgen05.ld.red.sync.aligned.32x32b.x16.max.u32 " FPS_T16 ", %3, [%9];\n"
-      " tcgen05.ld.red.sync.aligned.32x32b.x16.max.u32 " FPS_T16 ", %4, [%10];\n"
-      " tcgen05.ld.red.sync.aligned.32x32b.x16.max.u32 " FPS_T16 ", %5, [%11];\n}\n"
-      : "=r"(ma), "=r"(a1), "=r"(mb), "=r"(b1), "=r"(mc), "=r"(c1)
-      : "r"(a), "r"(a + 16), "r"(b), "r"(b + 16), "r"(c), "r"(c + 16)
+      " tcgen05.ld.red.sync.aligned.32x32b.x16.max.u32 " FPS_T16 ", %0, [%4];\n"
+      " tcgen05.ld.red.sync.aligned.32x32b.x16.max.u32 " FPS_T16 ", %1, [%5];\n"
+      " tcgen05.ld.red.sync.aligned.32x32b.x16.max.u32 " FPS_T16 ", %2, [%6];\n"
+      " tcgen05.ld.red.sync.aligned.32x32b.x16.max.u32 " FPS_T16 ", %3, [%7];\n}\n"
+      : "=r"(m0), "=r"(m1), "=r"(m2), "=r"(m3)
+      : "r"(a), "r"(a + 16), "r"(a + 32), "r"(a + 48)
       : "memory");
-  ma = max(ma, a1);
-  mb = max(mb, b1);
-  mc = max(mc, c1);
 #undef FPS_T16
+  return max(max(m0, m1), max(m2, m3));
 }
 
 // 32 consecutive TMEM columns of this thread's lane := w.
@@ -414,7 +413,13 @@ struct TcSmem {
   uint8_t b[F::kBStages][Geom<F>::kBTileBytes];
   uint64_t b_full[F::kBStages], b_empty[F::kBStages];
   uint64_t a_full[2], a_empty[2];
-  uint64_t acc_full[2], acc_empty[2];
+  uint64_t acc_full[F::kAccs], acc_empty[F::kAccs];
+  // (A parity wait cannot tell a phase from the one two before it.  Every epilogue warp
+  // takes every tile in order, so it waits for each accumulator's phases in order.  An MMA
+  // issuer takes every other tile: it reaches tile t only after the release of tile
+  // t - 2 - kAccs that its previous tile needed, which the in-order epilogue gives no
+  // earlier than that of tile t - 2 kAccs, the phase before the one tile t waits for.  So
+  // no wait ever runs two phases ahead.)
   uint64_t fin[2];                 // per MMA issuer: all of its MMAs complete
   uint32_t tmem_base;
   int bpos[kNumBuckets + 1];       // first layout position of each bucket
@@ -556,6 +561,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int i = 0; i < 2; ++i) {
       mbar_init(&S.a_full[i], 1);
       mbar_init(&S.a_empty[i], 2);   // both MMA issuers are done with the query tile
+    }
+    for (int i = 0; i < F::kAccs; ++i) {
       mbar_init(&S.acc_full[i], 1);
       mbar_init(&S.acc_empty[i], kEpiWarps);
     }
@@ -685,8 +692,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int64_t T = t0; T < t1; ++T, ++bn, ++tn) {
           if ((tn & 1u) != mine) continue;
           const int s = static_cast<int>(bn % F::kBStages);
-          const int acc = static_cast<int>(tn & 1);
-          if (!mbar_wait(&S.acc_empty[acc], ((tn >> 1) & 1) ^ 1, deadline) ||
+          const int acc = static_cast<int>(tn % F::kAccs);
+          if (!mbar_wait(&S.acc_empty[acc], ((tn / F::kAccs) & 1) ^ 1, deadline) ||
               !mbar_wait(&S.b_full[s], (bn / F::kBStages) & 1, deadline)) {
             ok = false;
             break;
@@ -753,7 +760,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       // per-row word is read every 4 tiles
       uint32_t gthr = thr;
       for (int T = t0; T < t1; ++T, ++tn) {
-        const int acc = static_cast<int>(tn & 1);
+        const int acc = static_cast<int>(tn % F::kAccs);
+        const uint32_t acc_par = (tn / F::kAccs) & 1;
         if (live && ((T - t0) & 3) == 0) {   // the refresher may have tightened this row's bound
           const unsigned long long w = *reinterpret_cast<volatile unsigned long long*>(&S.thr_w[row]);
           if ((w >> 32) == static_cast<unsigned long long>(j)) {
@@ -785,7 +793,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           // 128 half .. +127 as two groups of 64 FP16 values (pack::16b)
           advance(tpos);
           const bool act = live && static_cast<uint32_t>(abs(bk - pq)) <= thr;
-          const bool landed = mbar_wait(&S.acc_full[acc], (tn >> 1) & 1, deadline);
+          const bool landed = mbar_wait(&S.acc_full[acc], acc_par, deadline);
           if (!__all_sync(kFull, landed)) {   // one verdict for the whole warp
             ok = false;
             break;
@@ -820,78 +828,48 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
           }
         } else {
-          // FP4: a 192-record tile may span two buckets (boundaries fall on multiples of 64
-          // columns); this warp reads group A = columns 64 half .. +63 and group B =
-          // columns 128 + 32 half .. +31, each inside one bucket, as FP32 values
-          const int pA = tpos + 64 * half, pB = tpos + 128 + 32 * half;
-          advance(pA);
-          const int bkA = bk;
-          advance(pB);
-          const int bkB = bk;
-          const bool actA = live && static_cast<uint32_t>(abs(bkA - pq)) <= thr;
-          const bool actB = live && static_cast<uint32_t>(abs(bkB - pq)) <= thr;
-          const bool landed = mbar_wait(&S.acc_full[acc], (tn >> 1) & 1, deadline);
+          // FP4: a 128-record tile lies inside one bucket (buckets start at multiples of 256
+          // records); this warp takes columns 64 half .. +63 as one group.  The group's maximum
+          // comes from the TMEM loads themselves (tcgen05.ld.red); a group that passes (rare) is
+          // read again as values and goes to the ring before the accumulator is released --
+          // with three accumulators the MMA runs on while one warp hands off.
+          advance(tpos);
+          const bool act = live && static_cast<uint32_t>(abs(bk - pq)) <= thr;
+          const bool landed = mbar_wait(&S.acc_full[acc], acc_par, deadline);
           if (!__all_sync(kFull, landed)) {   // one verdict for the whole warp
             ok = false;
             break;
           }
           tc_fence_after();
-          // The maxima of group A (two 32-column halves) and group B come from the TMEM
-          // loads themselves (tcgen05.ld.red), one wait for all three.  A group that passes
-          // (rare) is read again as values and goes to the ring before the accumulator is
-          // released: keeping its values across the release costs more than the wait.
-          uint32_t needA16 = 0, needB16 = 0;
-          const uint32_t needA = bar_of(bkA, needA16), needB = bar_of(bkB, needB16);
-          if (__any_sync(kFull, actA || actB)) {
-            const uint32_t base = tmem + lane_addr + static_cast<uint32_t>(acc) * F::kAccStride;
-            uint32_t mA0, mA1, mB;
-            tmem_max3x32_nowait(base + 64 * half, base + 64 * half + 32, base + 128 + 32 * half, mA0, mA1, mB);
+          if (__any_sync(kFull, act)) {
+            uint32_t need16 = 0, need = 0;
+            if (act) need = bar_of(bk, need16);
+            const uint32_t base = tmem + lane_addr + static_cast<uint32_t>(acc) * F::kAccStride + 64u * half;
+            const uint32_t m = tmem_max64_nowait(base);
             tmem_wait_ld();
-            const bool passA = actA && max(mA0, mA1) >= needA;
-            const bool passB = actB && mB >= needB;
-            if (__any_sync(kFull, passA)) {
-              uint32_t hA[32];   // FP16 pairs (column 2i low, 2i + 1 high), read 32 columns at a time
+            const bool pass = act && m >= need;
+            if (__any_sync(kFull, pass)) {
+              uint32_t h[32];   // FP16 pairs (column 2i low, 2i + 1 high), read 32 columns at a time
               {
                 uint32_t v[32];
-                tmem_ld32_nowait(base + 64 * half, v);
+                tmem_ld32_nowait(base, v);
                 tmem_wait_ld();
 #pragma unroll
-                for (int i = 0; i < 16; ++i) hA[i] = half2_bits(v[2 * i], v[2 * i + 1]);
+                for (int i = 0; i < 16; ++i) h[i] = half2_bits(v[2 * i], v[2 * i + 1]);
               }
               {
                 uint32_t v[32];
-                tmem_ld32_nowait(base + 64 * half + 32, v);
+                tmem_ld32_nowait(base + 32, v);
                 tmem_wait_ld();
 #pragma unroll
-                for (int i = 0; i < 16; ++i) hA[16 + i] = half2_bits(v[2 * i], v[2 * i + 1]);
+                for (int i = 0; i < 16; ++i) h[16 + i] = half2_bits(v[2 * i], v[2 * i + 1]);
               }
-              if (passA) {
+              if (pass) {
                 auto fill = [&](RingEntry& e) {
 #pragma unroll
-                  for (int i = 0; i < 8; ++i)
-                    e.v[i] = make_uint4(hA[4 * i], hA[4 * i + 1], hA[4 * i + 2], hA[4 * i + 3]);
+                  for (int i = 0; i < 8; ++i) e.v[i] = make_uint4(h[4 * i], h[4 * i + 1], h[4 * i + 2], h[4 * i + 3]);
                 };
-                push(fill, needA16, bkA, pA, 64);
-              }
-            }
-            if (__any_sync(kFull, passB)) {
-              uint32_t hB[16];
-              {
-                uint32_t v[32];
-                tmem_ld32_nowait(base + 128 + 32 * half, v);
-                tmem_wait_ld();
-#pragma unroll
-                for (int i = 0; i < 16; ++i) hB[i] = half2_bits(v[2 * i], v[2 * i + 1]);
-              }
-              if (passB) {
-                auto fill = [&](RingEntry& e) {
-#pragma unroll
-                  for (int i = 0; i < 4; ++i) {
-                    e.v[i] = make_uint4(hB[4 * i], hB[4 * i + 1], hB[4 * i + 2], hB[4 * i + 3]);
-                    e.v[4 + i] = make_uint4(0u, 0u, 0u, 0u);
-                  }
-                };
-                push(fill, needB16, bkB, pB, 32);
+                push(fill, need16, bk, tpos + 64 * half, 64);
               }
             }
           }
@@ -1216,8 +1194,8 @@ cudaError_t tc_scan(int fmt, const DevLib& lib, const BatchDev& b, const uint8_t
                        : launch_tc<Fp8>(lib, b, lib_op, q_op, n_qt, num_sms, chunk, timeout_s, s);
 }
 
-// Library tiles per work item: 64 x 256 records (FP8), 96 x 192 records (FP4) -- about
+// Library tiles per work item: 64 x 256 records (FP8), 128 x 128 records (FP4) -- about
 // 16 K records, so that the query tiles of a chunk reuse it from L2.
-int tc_default_chunk(int fmt) { return fmt == kTcFp4 ? 96 : 64; }
+int tc_default_chunk(int fmt) { return fmt == kTcFp4 ? 128 : 64; }
 
 }  // namespace fps

@@ -1,12 +1,12 @@
 """Parity of the tensor-core batched paths (tcgen05) with the CPU oracle: 0/1 FP8 operands
 (kind::f8f6f4, FP16 accumulators, 256-record tiles) and packed 0/1 FP4 operands with unit block
-scales (kind::mxf4, FP32 accumulators, 192-record tiles).
+scales (kind::mxf4, FP32 accumulators, 128-record tiles, three accumulators).
 
 The contraction is exact (0/1 products, integer sums <= 166, which both accumulator types
 represent exactly), so the results must equal the oracle's element by element.  The ties case
 (20,000 identical records) drives many accepted records through the epilogue's hand-off ring at
 once.  Library sizes span one to many tiles of either format, with ragged last tiles and
-buckets that start inside a 192-record FP4 tile.
+buckets that end inside a tile.
 """
 import numpy as np
 import pytest

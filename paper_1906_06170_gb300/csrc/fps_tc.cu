@@ -163,6 +163,14 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                "l"(src), "r"(bytes), "r"(smem_addr(bar))
                : "memory");
 }
+// Same, with an L2 cache policy (createpolicy) for the copied lines.
+__device__ __forceinline__ void bulk_g2s_hint(void* dst, const void* src, uint32_t bytes, uint64_t* bar, uint64_t pol) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(pol)
+      : "memory");
+}
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -615,6 +623,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 0) {
     // ------------------------------------------------------------- producer
     if (lane == 0) {
+      // library tiles are read by every query tile of their chunk: keep them in L2 (evict last)
+      uint64_t pol_b;
+      asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol_b));
       uint32_t bn = 0;  // library tiles issued so far
       uint32_t na = 0;  // query tiles issued so far
       for (int64_t j = 0; ok; ++j) {
@@ -643,7 +654,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           constexpr int kPart = G::kBTileBytes / F::kBParts;
 #pragma unroll
           for (int part = 0; part < F::kBParts; ++part)
-            bulk_g2s(S.b[s] + part * kPart, src + part * kPart, kPart, &S.b_full[s]);
+            bulk_g2s_hint(S.b[s] + part * kPart, src + part * kPart, kPart, &S.b_full[s], pol_b);
         }
       }
       // wait (bounded) for copies still in flight before anyone leaves

@@ -549,12 +549,12 @@ def latency_entry(n: int, steps: int, warmup: int) -> dict:
     e2e = np.array(e2e)
     assert len(res_i) == min(K, n) and np.all(np.diff(res_d) >= 0), "latency results malformed"
     del scratch
-    # The library's kernel: up to 16 layout positions per thread of a 512-thread-per-SM grid and
+    # The library's kernel: up to 8 layout positions per thread of a 1024-thread-per-SM grid and
     # k <= 128 take the one-wave small-library scan, which reads every record (24 B each; it also
     # reads a 4 B index per position); the streaming scan reads only the buckets within the k-th
     # distance of the query.
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    one_wave = info["n_tiles"] * 128 <= 16 * sms * 512 and K <= 128
+    one_wave = info["n_tiles"] * 128 <= 8 * sms * 1024 and K <= 128
     if one_wave:
         kernel, alg = "scan_small_kernel", 24.0 * n + 8.0 * K
     else:

@@ -794,7 +794,7 @@ constexpr int kLargeWarps = 8, kLargeCap = 2048;   // k <= 1920
 // ------------------------------------------------------------ small libraries
 // A library whose layout has at most kSmPer positions per thread of a grid of
 // kSmThreads-thread blocks (about 1.2 M records on 152 SMs) is scanned in one
-// wave, without the bucket order: with a dozen records per thread, the fixed
+// wave, without the bucket order: with a handful of records per thread, the fixed
 // costs of the streaming kernel (visit-order tables, copy rings, running
 // bounds, two global atomics per block) are most of a query's time.
 //   1. thread t computes the distances of layout positions t, t + T, t + 2T, ...
@@ -811,12 +811,12 @@ constexpr int kLargeWarps = 8, kLargeCap = 2048;   // k <= 1920
 //      room, in which case the records at T are read again from the library.
 //      The k-th smallest candidate distance is T; the keys below it plus the
 //      smallest indices at T, sorted, are the answer (Fig. 3's first k rows).
-constexpr int kSmThreads = 512;
-constexpr int kSmPer = 16;                  // layout positions per thread
+constexpr int kSmThreads = 1024;
+constexpr int kSmPer = 8;                   // layout positions per thread
 constexpr int kSmMaxK = 128;                // largest k served
 constexpr int kSmRegion = 2048;             // keys per block: [0, kSmMaxK) below T_b, then those at T_b
 constexpr int kSmTieRoom = kSmRegion - kSmMaxK;
-constexpr int kSmTieCap = 16384;            // keys at T sorted in shared memory by the merge
+constexpr int kSmTieCap = 2048;             // keys at T sorted in shared memory by the merge
 constexpr size_t kSmSmem = static_cast<size_t>(kSmMaxK + kSmTieCap) * sizeof(unsigned long long);
 static_assert(kSmRegion <= kSmallWarps * (kSmallCap - kTile), "a block's region fits the candidate array");
 
